@@ -1,0 +1,329 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the batched FORA SSPPR query on one GB300 (or N replicas).
+
+Workload (default ``rmat20_deg16``): directed R-MAT graph, n = 2^20, average
+out-degree 16 (0.57, 0.19, 0.19, 0.05), dangling nodes fixed with one uniform
+edge; alpha = 0.2, eps = 0.5, delta = p_f = 1/n, r_max by the rule of Section
+3.2, 256 uniform sources per launch, top-500 per source.  A step is one batched
+query of 256 sources: push rounds, walk phase, estimate and top-k, all on the
+device; the graph stays resident and each step draws new sources.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on the
+host cores instead (a bounded sample of the same workload per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SSPPR queries/s and p99 latency at ε=0.5, batched+learned r_max vs plain FORA"
+UNIT = "queries/s"
+WALK_BYTES_PER_MOVE = 12      # row_ptr pair (8 B) + col entry (4 B)
+WALK_BYTES_PER_WALK = 24      # count RMW (4+4 B) + acc RMW (8+8 B)
+WALK_BYTES_PER_ENTRY = 24     # residual entry, offset, weight (8 B each)
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["fora", "reference"], default="fora")
+    ap.add_argument("--workload", default="rmat20_deg16")
+    ap.add_argument("--batch", type=int, default=None)
+    ap.add_argument("--k", type=int, default=None)
+    ap.add_argument("--eps", type=float, default=0.5)
+    ap.add_argument("--cpu-sources", type=int, default=8,
+                    help="sources in the bounded CPU-oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    import inputs
+    w = dict(inputs.WORKLOADS[args.workload])
+    if args.batch:
+        w["n_sources"] = args.batch
+    if args.k:
+        w["k"] = args.k
+    return w
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.index), "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, f[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        finally:
+            os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(path))["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profiled_traffic(kernel, wl):
+    """DRAM bytes per launch from a committed ncu summary (profiles/<kernel>_<wl>.txt,
+    line 'dram_bytes_per_launch: <int>'), or None."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{wl}.txt")
+    try:
+        for line in open(path):
+            if line.startswith("dram_bytes_per_launch:"):
+                return int(float(line.split(":", 1)[1]))
+    except Exception:
+        pass
+    return None
+
+
+def cpu_oracle_sample(rp, col, sources, w, eps, threads):
+    """The oracle as it stands on the host cores: wall time of `sources` queries."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(lambda s: oracle.ssppr(rp, col, int(s), eps=eps, k=w["k"]), sources))
+    return time.perf_counter() - t0
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    """CPU oracle arm: each step is a bounded sample of the workload on the host cores."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import inputs
+    import oracle
+    oracle.build()
+    w = workload(args)
+    rp, col = inputs.rmat_csr(w["scale"], w["avg_deg"], w["graph_seed"])
+    n = len(rp) - 1
+    threads = max(1, min(os.cpu_count() or 1, 4))
+    per_step = threads
+    for i in range(args.warmup):
+        src = inputs.uniform_sources(n, per_step, inputs.SOURCE_SEED + 7919 * (i + 1))
+        cpu_oracle_sample(rp, col, src, w, args.eps, threads)
+    times = []
+    for i in range(args.steps):
+        src = inputs.uniform_sources(n, per_step, inputs.SOURCE_SEED + 104729 * (i + 1))
+        times.append(cpu_oracle_sample(rp, col, src, w, args.eps, threads))
+    total = sum(times)
+    value = per_step * args.steps / total
+    sample = (f"{per_step} sources per step of the {args.workload} workload (top-{w['k']}, "
+              f"eps={args.eps}), one oracle query per thread")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "m": int(rp[-1]),
+                       "sources_per_step": per_step, "k": w["k"], "eps": args.eps,
+                       "alpha": 0.2, "delta": "1/n", "pf": "1/n", "rmax": "rule"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_fora(args):
+    import numpy as np
+    import torch
+
+    import inputs
+    world, rank, local = dist_setup()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1908_10583_gb300 import build as fbuild
+    fbuild.build()
+    import paper_1908_10583_gb300 as fora
+
+    w = workload(args)
+    B, k = w["n_sources"], w["k"]
+    rp, col = inputs.rmat_csr(w["scale"], w["avg_deg"], w["graph_seed"])
+    n = len(rp) - 1
+    g = fora.Graph(rp, col)
+    params = fora.Params.make(eps=args.eps, k=k, seed=inputs.WALK_SEED)
+    stream = torch.cuda.current_stream()
+    ids = torch.empty((B, k), dtype=torch.int32, device="cuda")
+    vals = torch.empty((B, k), dtype=torch.float64, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
+
+    def sources(step):
+        return inputs.uniform_sources(n, B, inputs.SOURCE_SEED + 1_000_003 * rank + 7919 * step)
+
+    for i in range(args.warmup):
+        g.ssppr_batch(sources(-1 - i), params, out_ids=ids, out_vals=vals, stream=stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    step_ms, walk_ms, walk_bytes, launches = [], [], [], 0
+    phase = {"ms_push": 0.0, "ms_residual": 0.0, "ms_walk": 0.0, "ms_topk": 0.0}
+    walks_total = steps_total = 0
+    for step in range(args.steps):
+        src = sources(step)
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, _, st = g.ssppr_batch(src, params, out_ids=ids, out_vals=vals, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        rounds = max(s.push_rounds for s in st)
+        launches += 2 * rounds + 1 + 3 + 1 + 1 + 19
+        for key in phase:
+            phase[key] += getattr(st[0], key)
+        walk_ms.append(st[0].ms_walk)
+        nw = sum(s.walks for s in st)
+        ns = sum(s.walk_steps for s in st)
+        nr = sum(s.residual_nodes for s in st)
+        walks_total += nw
+        steps_total += ns
+        walk_bytes.append(WALK_BYTES_PER_MOVE * ns + WALK_BYTES_PER_WALK * nw +
+                          WALK_BYTES_PER_ENTRY * nr)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = B * args.steps * world / (total_ms / 1e3)
+
+    # end to end through the public API: host sources in, host results out
+    h_ids = torch.empty((B, k), dtype=torch.int32, pin_memory=True).numpy()
+    h_vals = torch.empty((B, k), dtype=torch.float64, pin_memory=True).numpy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for step in range(args.steps):
+        g.ssppr_batch_host(sources(10_000 + step), params, h_ids, h_vals, stream=stream)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": B * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": B * (4 + 8),
+           "d2h_bytes_per_step": B * k * (4 + 8)}
+
+    peak, peak_kind = measured_peak_hbm()
+    achieved = (sum(walk_bytes) / len(walk_bytes)) / (statistics.mean(walk_ms) / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_walks", "achieved": achieved, "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": profiled_traffic("k_walks", args.workload),
+                "algorithmic_bytes_per_launch": sum(walk_bytes) / len(walk_bytes)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = max(1, min(os.cpu_count() or 1, args.cpu_sources))
+        src = inputs.uniform_sources(n, args.cpu_sources, inputs.SOURCE_SEED + 424242)
+        secs = cpu_oracle_sample(rp, col, src, w, args.eps, threads)
+        cpu = {"value": args.cpu_sources / secs, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{args.cpu_sources} sources of the {args.workload} workload "
+                         f"(top-{k}, eps={args.eps}), one oracle query per thread"}
+
+    lat = sorted(step_ms)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "m": int(rp[-1]),
+                       "avg_out_degree": w["avg_deg"], "sources_per_launch": B, "k": k,
+                       "eps": args.eps, "alpha": 0.2, "delta": "1/n", "pf": "1/n",
+                       "rmax": "rule", "parallelism": f"replicas{world}",
+                       "l2": "512 MiB buffer written between timed steps"},
+            "latency_ms": {"p50": lat[len(lat) // 2],
+                           "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                           "note": "every query of a batch completes with its batch"},
+            "phase_ms_per_step": {k_: v / args.steps for k_, v in phase.items()},
+            "walks_per_step": walks_total / args.steps,
+            "walk_moves_per_step": steps_total / args.steps,
+            "gpu_launches": launches,
+            "roofline": roofline,
+            "e2e": e2e,
+            "clocks": clk}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    g.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_fora(args)
+
+
+if __name__ == "__main__":
+    main()

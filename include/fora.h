@@ -1,0 +1,188 @@
+/*
+ * fora.h -- C ABI of the GB300 (sm_103a) implementation of the index-free
+ * FORA single-source Personalized PageRank (SSPPR) query of Wang et al.,
+ * "Efficient Algorithms for Approximate Single-Source Personalized PageRank
+ * Queries" (TODS 2019).
+ *
+ * A query from source s (Section 2.1, Def. 1 and Def. 2) runs:
+ *   1. Forward Push (Alg. 1) with residue threshold r_max, as synchronous
+ *      rounds: round t takes every node v with r(v) > r_max * d_out(v),
+ *      moves alpha * r(v) into its reserve, zeroes r(v), then adds
+ *      (1 - alpha) * r(v) / d_out(v) to the residue of every out-neighbour
+ *      (edges counted with multiplicity); residue that reaches a node of
+ *      round t during round t waits for round t + 1;
+ *   2. the walk phase of Alg. 2: omega_v = ceil(r(v) * C) alpha-terminating
+ *      random walks from every v with r(v) > 0, where
+ *      C = omega / r_sum = (2 eps/3 + 2) ln(2/p_f) / (eps^2 delta), each walk
+ *      adding r(v)/omega_v to the estimate of the node where it stops;
+ *   3. the estimate pi_hat(t) = reserve(t) + sum of walk weights ending at t,
+ *      and the k nodes with the largest pi_hat (ties: smaller id first).
+ * r_max defaults to the rule of Section 3.2 (Eq. rmax, with the Case 2
+ * fallback when m * r_max > 1).
+ *
+ * Random numbers: walk j from node v of source s reads the 32-bit words of
+ * Philox4x32-10 (Salmon et al., SC'11) blocks with counter (c, j, v, s),
+ * c = 0, 1, 2, ..., and key (seed & 0xffffffff, seed >> 32), in order.  At
+ * each node the walk takes one word u and stops if u < floor(alpha * 2^32);
+ * otherwise it draws a neighbour index in [0, d_out) by Lemire's
+ * multiply-and-reject method (one word per try).  Walk weights r(v)/omega_v
+ * are summed as unsigned 64-bit fixed point with 63 fractional bits
+ * (W_v = rint(r(v)/omega_v * 2^63)), so results do not depend on the order
+ * in which walks finish; pi_hat(t) = reserve(t) + acc(t) * 2^-63.
+ *
+ * Conventions for every entry point:
+ *   - return FORA_OK (0) or a negative FORA_ERR_* code; nothing is thrown
+ *     across the ABI; fora_last_error() gives a message for the calling
+ *     thread's last failure;
+ *   - output buffers are allocated by the caller;
+ *   - `stream` is a cudaStream_t owned by the caller (NULL = legacy default
+ *     stream); unless FORA_ASYNC is set the call returns after the stream
+ *     has finished the query;
+ *   - a graph handle serialises the queries issued on it (one workspace per
+ *     handle; concurrent calls on the same handle wait for each other).
+ */
+#ifndef FORA_H_
+#define FORA_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define FORA_OK 0
+#define FORA_ERR_BAD_ARG (-1)            /* invalid argument or CSR */
+#define FORA_ERR_DANGLING (-2)           /* a node with d_out = 0 (walks need d_out >= 1) */
+#define FORA_ERR_OOM (-3)                /* device allocation failed */
+#define FORA_ERR_WALK_OVERFLOW (-4)      /* a source needs >= 2^32 walks */
+#define FORA_ERR_PUSH_NOT_CONVERGED (-5) /* push exceeded FORA_MAX_PUSH_ROUNDS rounds */
+#define FORA_ERR_WALK_CAP (-6)           /* a walk exceeded FORA_MAX_WALK_STEPS moves */
+#define FORA_ERR_CUDA (-7)               /* a CUDA runtime call failed */
+
+#define FORA_MAX_PUSH_ROUNDS 100000
+#define FORA_MAX_WALK_STEPS 16384
+#define FORA_MAX_K 4096
+
+/* ---- flags of fora_params.flags ---- */
+#define FORA_OUT_DEVICE 0x1u /* out_ids / out_vals are device pointers (else host) */
+#define FORA_ASYNC 0x2u      /* return without synchronising (needs FORA_OUT_DEVICE and
+                                no stats); errors found on the device are then not reported */
+
+typedef struct fora_graph fora_graph; /* opaque: device copy of the CSR + query workspace */
+
+/* Query parameters (Def. 1; Alg. 2; Section 3.2). */
+typedef struct {
+  double alpha;  /* stop probability of a walk, 0 < alpha < 1 */
+  double eps;    /* relative error bound, > 0 */
+  double delta;  /* PPR threshold of Def. 1; <= 0 selects 1/n */
+  double pf;     /* failure probability, 0 < pf < 1; <= 0 selects 1/n */
+  double rmax;   /* residue threshold of Alg. 1; <= 0 selects the rule of Section 3.2 */
+  uint32_t k;    /* top-k size, 0 <= k <= min(n, FORA_MAX_K) */
+  uint32_t flags;
+  uint64_t seed; /* Philox key of the walk phase */
+} fora_params;
+
+/* Per-source counters of one query. */
+typedef struct {
+  double rmax;             /* residue threshold used */
+  double rsum;             /* sum of residues after the push */
+  uint64_t pushes;         /* node pushes over all rounds */
+  uint64_t edge_pushes;    /* sum of d_out over pushed nodes */
+  uint64_t residual_nodes; /* nodes with r(v) > 0 after the push */
+  uint64_t walks;          /* sum of omega_v */
+  uint64_t walk_steps;     /* moves over all walks */
+  uint32_t push_rounds;    /* rounds in which this source pushed at least one node */
+  int32_t source;
+  /* phase times of the whole call (the same for every source of a batch): push rounds,
+     residual compaction + walk offsets, walk kernel, estimate + top-k */
+  float ms_push, ms_residual, ms_walk, ms_topk;
+} fora_stats;
+
+/*
+ * Copy a CSR graph to the device.  row_ptr (n+1 entries, row_ptr[0] = 0,
+ * non-decreasing) and col (row_ptr[n] entries in [0, n)) are HOST arrays;
+ * they are copied and stay owned by the caller.  Requires 1 <= n < 2^31,
+ * m = row_ptr[n] < 2^32 and d_out(v) >= 1 for every v (FORA_ERR_DANGLING).
+ * Edges are taken with multiplicity; self-loops are allowed.  flags: 0.
+ */
+int fora_graph_create(int64_t n, const int64_t *row_ptr, const int32_t *col, uint32_t flags,
+                      fora_graph **out);
+
+/* Release the graph and its workspace.  NULL is accepted. */
+void fora_graph_destroy(fora_graph *g);
+
+/* n, m and the largest out-degree of a graph. */
+int fora_graph_info(const fora_graph *g, int64_t *n, int64_t *m, int64_t *max_degree);
+
+/*
+ * Resolve the parameters as a query would: the r_max in use (rule of
+ * Section 3.2 when params->rmax <= 0), C = omega / r_sum of Alg. 2 line 3,
+ * and the walk stop threshold floor(alpha * 2^32).  Any output may be NULL.
+ */
+int fora_resolve_params(const fora_graph *g, const fora_params *params, double *rmax,
+                        double *walk_scale, uint32_t *alpha_threshold);
+
+/*
+ * One SSPPR query from `source`: writes the top-k ids (int32) and
+ * estimates (double) to out_ids[k] / out_vals[k] (host pointers, or device
+ * pointers with FORA_OUT_DEVICE).  stats may be NULL.
+ */
+int fora_ssppr(fora_graph *g, const fora_params *params, int32_t source, int32_t *out_ids,
+               double *out_vals, fora_stats *stats, void *stream);
+
+/*
+ * nsrc independent queries in one launch sequence (all sources advance the
+ * push rounds together; the walks of all sources share one flat index space).
+ * sources: HOST array of nsrc ids.  out_ids / out_vals: [nsrc][k] row-major.
+ * stats: NULL or [nsrc].  Every source gives bit for bit the walk counts and
+ * top-k it would give alone (same Philox counters), up to the FP64 rounding
+ * order of the push.  The workspace for nsrc sources (about 52 bytes per
+ * source and node) is allocated on the first call that needs it and kept.
+ */
+int fora_ssppr_batch(fora_graph *g, const fora_params *params, const int32_t *sources,
+                     int32_t nsrc, int32_t *out_ids, double *out_vals, fora_stats *stats,
+                     void *stream);
+
+/* ---- inspection entry points (parity testing) ---- */
+
+/* Device arrays of a batch, [nsrc][n] row-major; any may be NULL. */
+typedef struct {
+  double *reserve;   /* pi_o after the push (input with FORA_DBG_GIVEN_PUSH) */
+  double *residue;   /* r after the push (input with FORA_DBG_GIVEN_PUSH) */
+  uint32_t *count;   /* walks ending at each node */
+  uint64_t *acc;     /* fixed-point walk weight ending at each node (2^-63 units) */
+  double *estimate;  /* pi_hat */
+} fora_debug_io;
+
+#define FORA_DBG_GIVEN_PUSH 0x1u /* skip the push; take reserve/residue from dbg (device) */
+
+/*
+ * fora_ssppr_batch with access to the intermediate arrays: with
+ * FORA_DBG_GIVEN_PUSH the walk phase and top-k run on the caller's reserve
+ * and residue (e.g. the oracle's); the other arrays are filled on return.
+ */
+int fora_ssppr_batch_debug(fora_graph *g, const fora_params *params, const int32_t *sources,
+                           int32_t nsrc, int32_t *out_ids, double *out_vals, fora_stats *stats,
+                           const fora_debug_io *dbg, uint32_t dbg_flags, void *stream);
+
+/*
+ * Top-k select on the device: for each of nrows rows of est ([nrows][n]
+ * device doubles, all >= 0), the k largest entries with ties to the smaller
+ * index, written to out_ids / out_vals ([nrows][k], device).  Uses scratch
+ * memory that the call allocates (stream-ordered) and frees.
+ */
+int fora_topk(const double *est, int64_t n, int32_t nrows, uint32_t k, int32_t *out_ids,
+              double *out_vals, void *stream);
+
+/* Evaluate the device Philox4x32-10 on count (counter[4], key[2]) rows of
+ * ctr_key (host, [count][6]); writes out (host, [count][4]). */
+int fora_philox_debug(const uint32_t *ctr_key, uint32_t *out, int32_t count);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char *fora_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FORA_H_ */

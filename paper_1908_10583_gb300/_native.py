@@ -1,0 +1,267 @@
+"""ctypes binding of ``libfora.so`` (include/fora.h): argument marshalling only.
+
+Every step of a query runs in the CUDA library; this module converts numpy
+arrays / torch tensors to pointers and checks return codes.  If the library
+has not been built, loading fails loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+FORA_OK = 0
+FORA_ERR_BAD_ARG = -1
+FORA_ERR_DANGLING = -2
+FORA_ERR_OOM = -3
+FORA_ERR_WALK_OVERFLOW = -4
+FORA_ERR_PUSH_NOT_CONVERGED = -5
+FORA_ERR_WALK_CAP = -6
+FORA_ERR_CUDA = -7
+FORA_MAX_K = 4096
+FORA_OUT_DEVICE = 0x1
+FORA_ASYNC = 0x2
+FORA_DBG_GIVEN_PUSH = 0x1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class FORAError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"fora error {code}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    """fora_params: alpha, eps, delta/pf (<= 0: 1/n), rmax (<= 0: rule), k, flags, seed."""
+    _fields_ = [("alpha", ctypes.c_double), ("eps", ctypes.c_double),
+                ("delta", ctypes.c_double), ("pf", ctypes.c_double),
+                ("rmax", ctypes.c_double), ("k", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32), ("seed", ctypes.c_uint64)]
+
+    @classmethod
+    def make(cls, alpha=0.2, eps=0.5, delta=0.0, pf=0.0, rmax=0.0, k=50, flags=0, seed=0x5EED):
+        return cls(alpha, eps, delta, pf, rmax, k, flags, seed)
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("rmax", ctypes.c_double), ("rsum", ctypes.c_double),
+                ("pushes", ctypes.c_uint64), ("edge_pushes", ctypes.c_uint64),
+                ("residual_nodes", ctypes.c_uint64), ("walks", ctypes.c_uint64),
+                ("walk_steps", ctypes.c_uint64), ("push_rounds", ctypes.c_uint32),
+                ("source", ctypes.c_int32), ("ms_push", ctypes.c_float),
+                ("ms_residual", ctypes.c_float), ("ms_walk", ctypes.c_float),
+                ("ms_topk", ctypes.c_float)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class DebugIO(ctypes.Structure):
+    _fields_ = [("reserve", ctypes.c_void_p), ("residue", ctypes.c_void_p),
+                ("count", ctypes.c_void_p), ("acc", ctypes.c_void_p),
+                ("estimate", ctypes.c_void_p)]
+
+
+def lib_path() -> str:
+    return _build.LIB_PATH
+
+
+def load():
+    """Load libfora.so (build it first with ``paper_1908_10583_gb300.build.build()``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB_PATH):
+            raise RuntimeError(f"{_build.LIB_PATH} is missing: the CUDA library must be built "
+                               "(paper_1908_10583_gb300.build.build()); there is no CPU fallback")
+        L = ctypes.CDLL(_build.LIB_PATH)
+        P, I, i64, i32, u32 = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int32,
+                               ctypes.c_uint32)
+        L.fora_graph_create.restype = I
+        L.fora_graph_create.argtypes = [i64, P, P, u32, ctypes.POINTER(P)]
+        L.fora_graph_destroy.restype = None
+        L.fora_graph_destroy.argtypes = [P]
+        L.fora_graph_info.restype = I
+        L.fora_graph_info.argtypes = [P, P, P, P]
+        L.fora_resolve_params.restype = I
+        L.fora_resolve_params.argtypes = [P, ctypes.POINTER(Params), P, P, P]
+        L.fora_ssppr.restype = I
+        L.fora_ssppr.argtypes = [P, ctypes.POINTER(Params), i32, P, P, P, P]
+        L.fora_ssppr_batch.restype = I
+        L.fora_ssppr_batch.argtypes = [P, ctypes.POINTER(Params), P, i32, P, P, P, P]
+        L.fora_ssppr_batch_debug.restype = I
+        L.fora_ssppr_batch_debug.argtypes = [P, ctypes.POINTER(Params), P, i32, P, P, P,
+                                             ctypes.POINTER(DebugIO), u32, P]
+        L.fora_topk.restype = I
+        L.fora_topk.argtypes = [P, i64, i32, u32, P, P, P]
+        L.fora_philox_debug.restype = I
+        L.fora_philox_debug.argtypes = [P, P, i32]
+        L.fora_last_error.restype = ctypes.c_char_p
+        L.fora_last_error.argtypes = []
+        _lib = L
+        return L
+
+
+def header_functions():
+    """Names of the functions include/fora.h declares (for the export check)."""
+    text = open(os.path.join(_build.INCLUDE, "fora.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fora_[a-z0-9_]+)\s*\(", text)))
+
+
+def _check(rc: int):
+    if rc != FORA_OK:
+        raise FORAError(rc, load().fora_last_error().decode(errors="replace"))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(x):
+    """Raw pointer of a numpy array or a torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+class Graph:
+    """A CSR graph resident on the current CUDA device (fora_graph_create)."""
+
+    def __init__(self, row_ptr, col):
+        L = load()
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        self.n = len(row_ptr) - 1
+        self.m = int(row_ptr[-1])
+        h = ctypes.c_void_p()
+        _check(L.fora_graph_create(self.n, row_ptr.ctypes.data, col.ctypes.data, 0,
+                                   ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().fora_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        n, m, d = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().fora_graph_info(self._h, ctypes.byref(n), ctypes.byref(m), ctypes.byref(d)))
+        return n.value, m.value, d.value
+
+    def resolve(self, params: Params):
+        r, c, t = ctypes.c_double(), ctypes.c_double(), ctypes.c_uint32()
+        _check(load().fora_resolve_params(self._h, ctypes.byref(params), ctypes.byref(r),
+                                          ctypes.byref(c), ctypes.byref(t)))
+        return r.value, c.value, t.value
+
+    def ssppr(self, source: int, params: Params, stream=None):
+        """One query; host outputs. Returns (ids, vals, Stats)."""
+        k = params.k
+        ids = np.zeros(k, dtype=np.int32)
+        vals = np.zeros(k, dtype=np.float64)
+        st = Stats()
+        p = Params.from_buffer_copy(params)
+        p.flags &= ~FORA_OUT_DEVICE
+        _check(load().fora_ssppr(self._h, ctypes.byref(p), int(source), ids.ctypes.data,
+                                 vals.ctypes.data, ctypes.addressof(st), _stream_ptr(stream)))
+        return ids, vals, st
+
+    def ssppr_batch(self, sources, params: Params, out_ids=None, out_vals=None, stats=True,
+                    stream=None):
+        """Batched query.  With out_ids/out_vals given (torch CUDA tensors [nsrc, k]) the
+        results stay on the device (FORA_OUT_DEVICE); otherwise numpy arrays are returned."""
+        src = np.ascontiguousarray(sources, dtype=np.int32)
+        nsrc, k = len(src), params.k
+        p = Params.from_buffer_copy(params)
+        if out_ids is not None:
+            p.flags |= FORA_OUT_DEVICE
+        else:
+            p.flags &= ~FORA_OUT_DEVICE
+            out_ids = np.zeros((nsrc, k), dtype=np.int32)
+            out_vals = np.zeros((nsrc, k), dtype=np.float64)
+        st = (Stats * nsrc)() if stats else None
+        _check(load().fora_ssppr_batch(self._h, ctypes.byref(p), src.ctypes.data, nsrc,
+                                       _ptr(out_ids), _ptr(out_vals),
+                                       ctypes.addressof(st) if st is not None else None,
+                                       _stream_ptr(stream)))
+        return out_ids, out_vals, (list(st) if st is not None else None)
+
+    def ssppr_batch_host(self, sources, params: Params, out_ids: np.ndarray,
+                         out_vals: np.ndarray, stream=None):
+        """Batched query into caller-provided host arrays ([nsrc, k] int32 / float64,
+        e.g. pinned); no stats."""
+        src = np.ascontiguousarray(sources, dtype=np.int32)
+        p = Params.from_buffer_copy(params)
+        p.flags &= ~FORA_OUT_DEVICE
+        assert out_ids.dtype == np.int32 and out_vals.dtype == np.float64
+        assert out_ids.size >= len(src) * p.k and out_vals.size >= len(src) * p.k
+        _check(load().fora_ssppr_batch(self._h, ctypes.byref(p), src.ctypes.data, len(src),
+                                       out_ids.ctypes.data, out_vals.ctypes.data, None,
+                                       _stream_ptr(stream)))
+        return out_ids, out_vals
+
+    def ssppr_batch_debug(self, sources, params: Params, dbg: dict, given_push=False,
+                          stream=None):
+        """Batched query exposing intermediate arrays.  dbg maps any of reserve, residue,
+        count, acc, estimate to torch CUDA tensors of shape [nsrc, n]."""
+        src = np.ascontiguousarray(sources, dtype=np.int32)
+        nsrc, k = len(src), params.k
+        p = Params.from_buffer_copy(params)
+        p.flags &= ~FORA_OUT_DEVICE
+        ids = np.zeros((nsrc, k), dtype=np.int32)
+        vals = np.zeros((nsrc, k), dtype=np.float64)
+        st = (Stats * nsrc)()
+        io = DebugIO(*[_ptr(dbg.get(f)) for f, _ in DebugIO._fields_])
+        _check(load().fora_ssppr_batch_debug(self._h, ctypes.byref(p), src.ctypes.data, nsrc,
+                                             ids.ctypes.data, vals.ctypes.data, ctypes.addressof(st),
+                                             ctypes.byref(io),
+                                             FORA_DBG_GIVEN_PUSH if given_push else 0,
+                                             _stream_ptr(stream)))
+        return ids, vals, list(st)
+
+
+def topk(est, k: int, out_ids=None, out_vals=None, stream=None):
+    """Top-k of each row of a [nrows, n] float64 CUDA tensor (fora_topk)."""
+    import torch
+    est = est.contiguous()
+    if est.dim() == 1:
+        est = est.unsqueeze(0)
+    nrows, n = est.shape
+    if out_ids is None:
+        out_ids = torch.empty((nrows, k), dtype=torch.int32, device=est.device)
+        out_vals = torch.empty((nrows, k), dtype=torch.float64, device=est.device)
+    _check(load().fora_topk(est.data_ptr(), n, nrows, k, out_ids.data_ptr(), out_vals.data_ptr(),
+                            _stream_ptr(stream)))
+    return out_ids, out_vals
+
+
+def philox(ctr_key: np.ndarray) -> np.ndarray:
+    """Device Philox4x32-10 on rows (ctr0..ctr3, key0, key1) -> [count, 4] words."""
+    ck = np.ascontiguousarray(ctr_key, dtype=np.uint32).reshape(-1, 6)
+    out = np.zeros((len(ck), 4), dtype=np.uint32)
+    _check(load().fora_philox_debug(ck.ctypes.data, out.ctypes.data, len(ck)))
+    return out

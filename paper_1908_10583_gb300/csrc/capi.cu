@@ -1,0 +1,452 @@
+// C ABI (include/fora.h) and the host side of the query engine: graph residency,
+// the per-graph workspace, and the phase sequence of a (batched) query.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "fora.h"
+#include "fora_engine.cuh"
+
+using namespace fora;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(e_ == cudaErrorMemoryAllocation ? FORA_ERR_OOM : FORA_ERR_CUDA,        \
+                  "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__,      \
+                  __LINE__);                                                             \
+  } while (0)
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+}  // namespace
+
+struct fora_graph {
+  int64_t n = 0, m = 0, max_deg = 0;
+  uint64_t hub_chunks = 0;  // sum over nodes with d > kHubChunk of ceil(d / kHubChunk)
+  uint32_t* row = nullptr;
+  int32_t* col = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  std::mutex mu;
+
+  // workspace for up to `cap` sources
+  int cap = 0;
+  double* r = nullptr;
+  double* res = nullptr;
+  uint32_t* cnt = nullptr;
+  unsigned long long* acc = nullptr;
+  unsigned long long* q[2] = {nullptr, nullptr};
+  unsigned long long* hub[2] = {nullptr, nullptr};
+  double* fa = nullptr;
+  unsigned long long* small = nullptr;  // counters[4] totals[2]
+  uint32_t* err = nullptr;
+  int32_t* sources = nullptr;
+  double* rmax = nullptr;
+  SlotStats* stats = nullptr;
+  unsigned long long* blk = nullptr;  // [2][residual_grid]
+  int residual_grid = 0;
+  void* topk_scratch = nullptr;
+  int32_t* out_ids = nullptr;  // device staging of host-bound results [cap][FORA_MAX_K]
+  double* out_vals = nullptr;
+  // pinned host mirrors
+  unsigned long long* h_counters = nullptr;
+  SlotStats* h_stats = nullptr;
+  uint32_t* h_err = nullptr;
+  int32_t* h_sources = nullptr;
+  double* h_rmax = nullptr;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+
+  void release_workspace() {
+    dfree(r); dfree(res); dfree(cnt); dfree(acc);
+    dfree(q[0]); dfree(q[1]); dfree(hub[0]); dfree(hub[1]); dfree(fa);
+    dfree(small); dfree(err); dfree(sources); dfree(rmax); dfree(stats); dfree(blk);
+    if (topk_scratch) cudaFree(topk_scratch);
+    topk_scratch = nullptr;
+    dfree(out_ids); dfree(out_vals);
+    if (h_counters) cudaFreeHost(h_counters);
+    if (h_stats) cudaFreeHost(h_stats);
+    if (h_err) cudaFreeHost(h_err);
+    if (h_sources) cudaFreeHost(h_sources);
+    if (h_rmax) cudaFreeHost(h_rmax);
+    h_counters = nullptr; h_stats = nullptr; h_err = nullptr; h_sources = nullptr; h_rmax = nullptr;
+    cap = 0;
+  }
+};
+
+namespace {
+
+int ensure_workspace(fora_graph* g, int nsrc) {
+  if (nsrc <= g->cap) return FORA_OK;
+  g->release_workspace();
+  const size_t N = (size_t)nsrc * (size_t)g->n;
+  const size_t H = (size_t)nsrc * g->hub_chunks + 1;
+  g->residual_grid = g->num_sms * 8;
+  CUDA_TRY(cudaMalloc(&g->r, N * sizeof(double)));
+  CUDA_TRY(cudaMalloc(&g->res, N * sizeof(double)));
+  CUDA_TRY(cudaMalloc(&g->cnt, N * sizeof(uint32_t)));
+  CUDA_TRY(cudaMalloc(&g->acc, N * sizeof(unsigned long long)));
+  CUDA_TRY(cudaMalloc(&g->q[0], (N + 1) * sizeof(unsigned long long)));
+  CUDA_TRY(cudaMalloc(&g->q[1], (N + 1) * sizeof(unsigned long long)));
+  CUDA_TRY(cudaMalloc(&g->fa, (N + 1) * sizeof(double)));
+  CUDA_TRY(cudaMalloc(&g->hub[0], H * sizeof(unsigned long long)));
+  CUDA_TRY(cudaMalloc(&g->hub[1], H * sizeof(unsigned long long)));
+  CUDA_TRY(cudaMalloc(&g->small, 8 * sizeof(unsigned long long)));
+  CUDA_TRY(cudaMalloc(&g->err, sizeof(uint32_t)));
+  CUDA_TRY(cudaMalloc(&g->sources, nsrc * sizeof(int32_t)));
+  CUDA_TRY(cudaMalloc(&g->rmax, nsrc * sizeof(double)));
+  CUDA_TRY(cudaMalloc(&g->stats, nsrc * sizeof(SlotStats)));
+  CUDA_TRY(cudaMalloc(&g->blk, 2 * (size_t)g->residual_grid * sizeof(unsigned long long)));
+  CUDA_TRY(cudaMalloc(&g->topk_scratch, topk_scratch_bytes(nsrc)));
+  CUDA_TRY(cudaMalloc(&g->out_ids, (size_t)nsrc * FORA_MAX_K * sizeof(int32_t)));
+  CUDA_TRY(cudaMalloc(&g->out_vals, (size_t)nsrc * FORA_MAX_K * sizeof(double)));
+  CUDA_TRY(cudaMallocHost(&g->h_counters, 8 * sizeof(unsigned long long)));
+  CUDA_TRY(cudaMallocHost(&g->h_stats, nsrc * sizeof(SlotStats)));
+  CUDA_TRY(cudaMallocHost(&g->h_err, sizeof(uint32_t)));
+  CUDA_TRY(cudaMallocHost(&g->h_sources, nsrc * sizeof(int32_t)));
+  CUDA_TRY(cudaMallocHost(&g->h_rmax, nsrc * sizeof(double)));
+  g->cap = nsrc;
+  return FORA_OK;
+}
+
+// Parameters as a query resolves them (Alg. 2 line 3; Eq. rmax and Case 2, Section 3.2).
+struct Resolved {
+  double alpha, eps, delta, pf, rmax, walk_scale;
+  uint32_t alpha_threshold;
+};
+
+int resolve(const fora_graph* g, const fora_params* p, Resolved* out) {
+  if (!g || !p) return fail(FORA_ERR_BAD_ARG, "null graph or params");
+  Resolved r;
+  r.alpha = p->alpha;
+  r.eps = p->eps;
+  r.delta = p->delta > 0 ? p->delta : 1.0 / (double)g->n;
+  r.pf = p->pf > 0 ? p->pf : 1.0 / (double)g->n;
+  if (!(r.alpha > 0.0 && r.alpha < 1.0)) return fail(FORA_ERR_BAD_ARG, "alpha must be in (0,1)");
+  if (!(r.eps > 0.0) || !std::isfinite(r.eps)) return fail(FORA_ERR_BAD_ARG, "eps must be > 0");
+  if (!(r.delta <= 1.0)) return fail(FORA_ERR_BAD_ARG, "delta must be in (0,1]");
+  if (!(r.pf < 1.0)) return fail(FORA_ERR_BAD_ARG, "pf must be in (0,1)");
+  const double m = (double)g->m;
+  // C = omega / r_sum = (2 eps/3 + 2) log(2/p_f) / (eps^2 delta)
+  r.walk_scale = ((2.0 * r.eps / 3.0 + 2.0) * log(2.0 / r.pf)) / (r.eps * r.eps * r.delta);
+  if (p->rmax > 0.0) {
+    r.rmax = p->rmax;
+  } else {
+    r.rmax = (r.eps / sqrt(m)) * sqrt(r.delta / ((2.0 * r.eps / 3.0 + 2.0) * log(2.0 / r.pf)));
+    if (m * r.rmax > 1.0)
+      r.rmax = (r.eps * r.eps * r.delta) / ((2.0 * r.eps / 3.0 + 2.0) * log(2.0 / r.pf));
+  }
+  if (!std::isfinite(r.walk_scale) || !std::isfinite(r.rmax))
+    return fail(FORA_ERR_BAD_ARG, "parameters give a non-finite r_max or walk count");
+  r.alpha_threshold = (uint32_t)floor(r.alpha * 4294967296.0);
+  *out = r;
+  return FORA_OK;
+}
+
+int run_batch(fora_graph* g, const fora_params* p, const int32_t* sources, int nsrc,
+              int32_t* out_ids, double* out_vals, fora_stats* st, const fora_debug_io* dbg,
+              uint32_t dbg_flags, cudaStream_t stream) {
+  Resolved rp;
+  int rc = resolve(g, p, &rp);
+  if (rc) return rc;
+  if (nsrc < 1 || !sources) return fail(FORA_ERR_BAD_ARG, "need at least one source");
+  if (nsrc > 65535) return fail(FORA_ERR_BAD_ARG, "at most 65535 sources per call");
+  if (p->k > FORA_MAX_K || (int64_t)p->k > g->n) return fail(FORA_ERR_BAD_ARG, "k out of range");
+  if (p->k > 0 && (!out_ids || !out_vals)) return fail(FORA_ERR_BAD_ARG, "null output");
+  const bool out_dev = (p->flags & FORA_OUT_DEVICE) != 0;
+  const bool async = (p->flags & FORA_ASYNC) != 0;
+  if (async && (!out_dev || st)) return fail(FORA_ERR_BAD_ARG, "FORA_ASYNC needs FORA_OUT_DEVICE and no stats");
+  const bool given = (dbg_flags & FORA_DBG_GIVEN_PUSH) != 0;
+  if (given && (!dbg || !dbg->reserve || !dbg->residue))
+    return fail(FORA_ERR_BAD_ARG, "FORA_DBG_GIVEN_PUSH needs reserve and residue arrays");
+  for (int i = 0; i < nsrc; ++i)
+    if (sources[i] < 0 || sources[i] >= g->n) return fail(FORA_ERR_BAD_ARG, "source %d out of range", i);
+
+  std::lock_guard<std::mutex> lock(g->mu);
+  CUDA_TRY(cudaSetDevice(g->device));
+  rc = ensure_workspace(g, nsrc);
+  if (rc) return rc;
+  const size_t N = (size_t)nsrc * (size_t)g->n;
+  for (int i = 0; i < nsrc; ++i) {
+    g->h_sources[i] = sources[i];
+    g->h_rmax[i] = rp.rmax;
+  }
+  CUDA_TRY(cudaMemcpyAsync(g->sources, g->h_sources, nsrc * sizeof(int32_t), cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(cudaMemcpyAsync(g->rmax, g->h_rmax, nsrc * sizeof(double), cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(cudaMemsetAsync(g->cnt, 0, N * sizeof(uint32_t), stream));
+  CUDA_TRY(cudaMemsetAsync(g->acc, 0, N * sizeof(unsigned long long), stream));
+  CUDA_TRY(cudaMemsetAsync(g->small, 0, 8 * sizeof(unsigned long long), stream));
+  CUDA_TRY(cudaMemsetAsync(g->err, 0, sizeof(uint32_t), stream));
+  CUDA_TRY(cudaMemsetAsync(g->stats, 0, nsrc * sizeof(SlotStats), stream));
+
+  GraphDev gd{g->n, g->m, g->row, g->col};
+  BatchDev b{};
+  b.nsrc = nsrc;
+  b.alpha = rp.alpha;
+  b.walk_scale = rp.walk_scale;
+  b.alpha_threshold = rp.alpha_threshold;
+  b.seed = p->seed;
+  b.r = g->r; b.res = g->res; b.cnt = g->cnt; b.acc = g->acc;
+  b.q[0] = g->q[0]; b.q[1] = g->q[1]; b.fa = g->fa;
+  b.hub[0] = g->hub[0]; b.hub[1] = g->hub[1];
+  b.counters = g->small;
+  b.totals = g->small + 4;
+  b.sources = g->sources; b.rmax = g->rmax; b.stats = g->stats; b.err = g->err;
+  b.wr_entry = g->q[0];
+  b.wr_offset = g->q[1];
+  b.wr_weight = reinterpret_cast<unsigned long long*>(g->fa);
+  b.blk_cnt = g->blk;
+  b.blk_walks = g->blk + g->residual_grid;
+  b.residual_grid = g->residual_grid;
+
+  const bool timed = st != nullptr;
+  if (timed) CUDA_TRY(cudaEventRecord(g->ev[0], stream));
+
+  // ---- push (Alg. 1) ----
+  if (given) {
+    CUDA_TRY(cudaMemcpyAsync(g->res, dbg->reserve, N * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    CUDA_TRY(cudaMemcpyAsync(g->r, dbg->residue, N * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  } else {
+    CUDA_TRY(cudaMemsetAsync(g->r, 0, N * sizeof(double), stream));
+    CUDA_TRY(cudaMemsetAsync(g->res, 0, N * sizeof(double), stream));
+    CUDA_TRY(launch_push_init(gd, b, stream));
+    CUDA_TRY(cudaMemcpyAsync(g->h_counters, g->small, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    int cur = 0;
+    uint32_t round = 0;
+    while (g->h_counters[cur * 2] > 0) {
+      if (++round > FORA_MAX_PUSH_ROUNDS)
+        return fail(FORA_ERR_PUSH_NOT_CONVERGED, "push did not converge in %d rounds", FORA_MAX_PUSH_ROUNDS);
+      CUDA_TRY(launch_push_round(gd, b, cur, g->h_counters[cur * 2], g->h_counters[cur * 2 + 1], round,
+                                 g->num_sms, stream));
+      const int nxt = cur ^ 1;
+      CUDA_TRY(cudaMemcpyAsync(g->h_counters + nxt * 2, g->small + nxt * 2, 2 * sizeof(unsigned long long),
+                               cudaMemcpyDeviceToHost, stream));
+      CUDA_TRY(cudaStreamSynchronize(stream));
+      cur = nxt;
+    }
+    if (dbg && dbg->reserve)
+      CUDA_TRY(cudaMemcpyAsync(dbg->reserve, g->res, N * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    if (dbg && dbg->residue)
+      CUDA_TRY(cudaMemcpyAsync(dbg->residue, g->r, N * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  }
+  if (timed) CUDA_TRY(cudaEventRecord(g->ev[1], stream));
+
+  // ---- walks (Alg. 2, lines 3-10) ----
+  CUDA_TRY(launch_residuals(gd, b, stream));
+  if (timed) CUDA_TRY(cudaEventRecord(g->ev[2], stream));
+  CUDA_TRY(launch_walks(gd, b, g->num_sms, stream));
+  if (timed) CUDA_TRY(cudaEventRecord(g->ev[3], stream));
+  if (dbg && dbg->count)
+    CUDA_TRY(cudaMemcpyAsync(dbg->count, g->cnt, N * sizeof(uint32_t), cudaMemcpyDeviceToDevice, stream));
+  if (dbg && dbg->acc)
+    CUDA_TRY(cudaMemcpyAsync(dbg->acc, g->acc, N * sizeof(uint64_t), cudaMemcpyDeviceToDevice, stream));
+
+  // ---- estimate and top-k (the residue array becomes the estimate) ----
+  CUDA_TRY(launch_estimate(g->res, g->acc, g->r, N, g->num_sms, stream));
+  if (dbg && dbg->estimate)
+    CUDA_TRY(cudaMemcpyAsync(dbg->estimate, g->r, N * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  int32_t* ids_dev = out_dev ? out_ids : g->out_ids;
+  double* vals_dev = out_dev ? out_vals : g->out_vals;
+  CUDA_TRY(launch_topk(g->r, g->n, nsrc, p->k, ids_dev, vals_dev,
+                       topk_scratch_carve(g->topk_scratch, nsrc), g->num_sms, stream));
+  if (timed) CUDA_TRY(cudaEventRecord(g->ev[4], stream));
+  if (!out_dev && p->k > 0) {
+    CUDA_TRY(cudaMemcpyAsync(out_ids, g->out_ids, (size_t)nsrc * p->k * sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaMemcpyAsync(out_vals, g->out_vals, (size_t)nsrc * p->k * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  }
+  if (async) return FORA_OK;
+  CUDA_TRY(cudaMemcpyAsync(g->h_err, g->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
+  if (st) CUDA_TRY(cudaMemcpyAsync(g->h_stats, g->stats, nsrc * sizeof(SlotStats), cudaMemcpyDeviceToHost, stream));
+  CUDA_TRY(cudaStreamSynchronize(stream));
+  if (*g->h_err & kErrWalkOverflow) return fail(FORA_ERR_WALK_OVERFLOW, "a source needs 2^32 or more walks");
+  if (*g->h_err & kErrWalkCap) return fail(FORA_ERR_WALK_CAP, "a walk exceeded %d moves", FORA_MAX_WALK_STEPS);
+  if (st) {
+    float ms[4] = {0, 0, 0, 0};
+    for (int i = 0; i < 4; ++i) CUDA_TRY(cudaEventElapsedTime(&ms[i], g->ev[i], g->ev[i + 1]));
+    for (int i = 0; i < nsrc; ++i) {
+      const SlotStats& s = g->h_stats[i];
+      fora_stats& o = st[i];
+      o.rmax = rp.rmax;
+      o.rsum = s.rsum;
+      o.pushes = s.pushes;
+      o.edge_pushes = s.edge_pushes;
+      o.residual_nodes = s.residual_nodes;
+      o.walks = s.walks;
+      o.walk_steps = s.walk_steps;
+      o.push_rounds = s.rounds;
+      o.source = sources[i];
+      o.ms_push = ms[0];
+      o.ms_residual = ms[1];
+      o.ms_walk = ms[2];
+      o.ms_topk = ms[3];
+    }
+  }
+  return FORA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fora_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col, uint32_t flags,
+                      fora_graph** out) {
+  if (!out) return fail(FORA_ERR_BAD_ARG, "null output handle");
+  *out = nullptr;
+  if (flags != 0) return fail(FORA_ERR_BAD_ARG, "unknown flags");
+  if (n < 1 || n > 0x7FFFFFFF || !row_ptr || !col) return fail(FORA_ERR_BAD_ARG, "bad n or null arrays");
+  if (row_ptr[0] != 0) return fail(FORA_ERR_BAD_ARG, "row_ptr[0] must be 0");
+  const int64_t m = row_ptr[n];
+  if (m < 1 || m > 0xFFFFFFFFll) return fail(FORA_ERR_BAD_ARG, "m must be in [1, 2^32)");
+  std::vector<uint32_t> row((size_t)n + 1);
+  int64_t max_deg = 0;
+  uint64_t hub_chunks = 0;
+  for (int64_t v = 0; v < n; ++v) {
+    const int64_t d = row_ptr[v + 1] - row_ptr[v];
+    if (d < 0 || row_ptr[v + 1] > m) return fail(FORA_ERR_BAD_ARG, "row_ptr not monotone at %lld", (long long)v);
+    if (d == 0) return fail(FORA_ERR_DANGLING, "node %lld has no out-edge", (long long)v);
+    if (d > max_deg) max_deg = d;
+    if ((uint64_t)d > kHubChunk) hub_chunks += ((uint64_t)d + kHubChunk - 1) / kHubChunk;
+    row[v] = (uint32_t)row_ptr[v];
+  }
+  row[n] = (uint32_t)m;
+  for (int64_t e = 0; e < m; ++e)
+    if (col[e] < 0 || col[e] >= n) return fail(FORA_ERR_BAD_ARG, "col[%lld] out of range", (long long)e);
+
+  fora_graph* g = new fora_graph();
+  g->n = n;
+  g->m = m;
+  g->max_deg = max_deg;
+  g->hub_chunks = hub_chunks;
+  auto bail = [&](int code) {
+    fora_graph_destroy(g);
+    return code;
+  };
+  if (cudaGetDevice(&g->device) != cudaSuccess) return bail(fail(FORA_ERR_CUDA, "no CUDA device"));
+  if (cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess)
+    return bail(fail(FORA_ERR_CUDA, "cannot query the SM count"));
+  cudaError_t e = cudaMalloc(&g->row, ((size_t)n + 1) * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&g->col, (size_t)m * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemcpy(g->row, row.data(), ((size_t)n + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->col, col, (size_t)m * sizeof(int32_t), cudaMemcpyHostToDevice);
+  for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = cudaEventCreate(&g->ev[i]);
+  if (e != cudaSuccess)
+    return bail(fail(e == cudaErrorMemoryAllocation ? FORA_ERR_OOM : FORA_ERR_CUDA, "graph upload: %s",
+                     cudaGetErrorString(e)));
+  *out = g;
+  return FORA_OK;
+}
+
+void fora_graph_destroy(fora_graph* g) {
+  if (!g) return;
+  {
+    std::lock_guard<std::mutex> lock(g->mu);
+    cudaSetDevice(g->device);
+    g->release_workspace();
+    dfree(g->row);
+    dfree(g->col);
+    for (int i = 0; i < 5; ++i)
+      if (g->ev[i]) cudaEventDestroy(g->ev[i]);
+  }
+  delete g;
+}
+
+int fora_graph_info(const fora_graph* g, int64_t* n, int64_t* m, int64_t* max_degree) {
+  if (!g) return fail(FORA_ERR_BAD_ARG, "null graph");
+  if (n) *n = g->n;
+  if (m) *m = g->m;
+  if (max_degree) *max_degree = g->max_deg;
+  return FORA_OK;
+}
+
+int fora_resolve_params(const fora_graph* g, const fora_params* params, double* rmax,
+                        double* walk_scale, uint32_t* alpha_threshold) {
+  Resolved r;
+  const int rc = resolve(g, params, &r);
+  if (rc) return rc;
+  if (rmax) *rmax = r.rmax;
+  if (walk_scale) *walk_scale = r.walk_scale;
+  if (alpha_threshold) *alpha_threshold = r.alpha_threshold;
+  return FORA_OK;
+}
+
+int fora_ssppr(fora_graph* g, const fora_params* params, int32_t source, int32_t* out_ids,
+               double* out_vals, fora_stats* stats, void* stream) {
+  return run_batch(g, params, &source, 1, out_ids, out_vals, stats, nullptr, 0, (cudaStream_t)stream);
+}
+
+int fora_ssppr_batch(fora_graph* g, const fora_params* params, const int32_t* sources, int32_t nsrc,
+                     int32_t* out_ids, double* out_vals, fora_stats* stats, void* stream) {
+  return run_batch(g, params, sources, nsrc, out_ids, out_vals, stats, nullptr, 0, (cudaStream_t)stream);
+}
+
+int fora_ssppr_batch_debug(fora_graph* g, const fora_params* params, const int32_t* sources,
+                           int32_t nsrc, int32_t* out_ids, double* out_vals, fora_stats* stats,
+                           const fora_debug_io* dbg, uint32_t dbg_flags, void* stream) {
+  return run_batch(g, params, sources, nsrc, out_ids, out_vals, stats, dbg, dbg_flags,
+                   (cudaStream_t)stream);
+}
+
+int fora_topk(const double* est, int64_t n, int32_t nrows, uint32_t k, int32_t* out_ids,
+              double* out_vals, void* stream) {
+  if (!est || n < 1 || n > 0x7FFFFFFF || nrows < 1) return fail(FORA_ERR_BAD_ARG, "bad arguments");
+  if (k > FORA_MAX_K || (int64_t)k > n) return fail(FORA_ERR_BAD_ARG, "k out of range");
+  if (k == 0) return FORA_OK;
+  if (!out_ids || !out_vals) return fail(FORA_ERR_BAD_ARG, "null output");
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  void* scratch = nullptr;
+  CUDA_TRY(cudaMallocAsync(&scratch, topk_scratch_bytes(nrows), st));
+  const cudaError_t e = launch_topk(est, n, nrows, k, out_ids, out_vals, topk_scratch_carve(scratch, nrows),
+                                    sms, st);
+  cudaFreeAsync(scratch, st);
+  CUDA_TRY(e);
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return FORA_OK;
+}
+
+int fora_philox_debug(const uint32_t* ctr_key, uint32_t* out, int32_t count) {
+  if (count < 0 || (count > 0 && (!ctr_key || !out))) return fail(FORA_ERR_BAD_ARG, "bad arguments");
+  if (count == 0) return FORA_OK;
+  uint32_t *d_in = nullptr, *d_out = nullptr;
+  CUDA_TRY(cudaMalloc(&d_in, (size_t)count * 6 * sizeof(uint32_t)));
+  cudaError_t e = cudaMalloc(&d_out, (size_t)count * 4 * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemcpy(d_in, ctr_key, (size_t)count * 6 * sizeof(uint32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_philox_table(d_in, d_out, count, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(out, d_out, (size_t)count * 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+  cudaFree(d_in);
+  cudaFree(d_out);
+  CUDA_TRY(e);
+  return FORA_OK;
+}
+
+const char* fora_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

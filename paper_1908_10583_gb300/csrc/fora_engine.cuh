@@ -1,0 +1,110 @@
+// Internal declarations of the FORA query engine (device state and kernel
+// launchers).  Not part of the C ABI (include/fora.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fora {
+
+// Nodes with more out-edges than this are pushed in chunks of this many edges,
+// one warp per chunk, so that a hub never serialises a round on one warp.
+constexpr uint32_t kHubChunk = 256;
+constexpr int kHubChunkBits = 24;  // hub item = (frontier index << 24) | chunk
+
+// Top-k radix select: 96-bit keys (estimate bits : ~id), 12-bit digits.
+constexpr int kDigitBits = 12;
+constexpr int kBins = 1 << kDigitBits;
+constexpr int kLevels = 96 / kDigitBits;
+constexpr uint32_t kSortCap = 8192;  // candidates sorted in shared memory at the end
+
+// Device error bits (ORed into BatchDev::err).
+constexpr uint32_t kErrWalkCap = 1u;
+constexpr uint32_t kErrWalkOverflow = 2u;
+
+struct GraphDev {
+  int64_t n;
+  int64_t m;
+  const uint32_t* row;  // [n+1] edge offsets (m < 2^32)
+  const int32_t* col;   // [m]
+};
+
+// Per-source counters kept on the device during a call.
+struct SlotStats {
+  unsigned long long pushes;
+  unsigned long long edge_pushes;
+  unsigned long long residual_nodes;
+  unsigned long long walks;
+  unsigned long long walk_steps;
+  double rsum;
+  uint32_t rounds;
+  uint32_t pad;
+};
+
+// Top-k select state of one row.
+struct TopkSlot {
+  unsigned long long pa;  // known bits of the key's upper 64 bits (estimate bits)
+  uint32_t pb;            // known bits of the key's lower 32 bits (~id)
+  uint32_t plen;          // number of leading key bits fixed so far
+  uint32_t kk;            // how many keys still to take from the current bucket
+  uint32_t done;
+  uint32_t ncand;
+  uint32_t pad;
+};
+
+// Pointers into a call's workspace; all arrays source-major ([slot][n]).
+struct BatchDev {
+  int32_t nsrc;
+  double alpha;
+  double walk_scale;         // C = omega / r_sum
+  uint32_t alpha_threshold;  // floor(alpha * 2^32)
+  uint64_t seed;
+  double* r;                 // residue, later the estimate
+  double* res;               // reserve
+  uint32_t* cnt;             // walk end counts
+  unsigned long long* acc;   // fixed-point walk weight (2^-63 units)
+  unsigned long long* q[2];  // frontier queues: (slot << 32) | v
+  double* fa;                // per frontier entry: (1 - alpha) r(v) / d(v)
+  unsigned long long* hub[2];  // hub chunk items
+  unsigned long long* counters;  // [4]: frontier/hub counts of parity 0 and 1
+  const int32_t* sources;    // [nsrc]
+  const double* rmax;        // [nsrc]
+  SlotStats* stats;          // [nsrc]
+  uint32_t* err;
+  // walk phase
+  unsigned long long* wr_entry;   // residual list: (slot << 32) | v   (aliases q[0])
+  unsigned long long* wr_offset;  // exclusive walk offsets, [|R| + 1]  (aliases q[1])
+  unsigned long long* wr_weight;  // fixed-point weight per walk        (aliases fa)
+  unsigned long long* blk_cnt;    // [grid] residual nodes per block, then block offsets
+  unsigned long long* blk_walks;  // [grid] walks per block, then block offsets
+  unsigned long long* totals;     // [2]: |R|, W
+  int residual_grid;
+};
+
+// push.cu
+cudaError_t launch_push_init(const GraphDev& g, const BatchDev& b, cudaStream_t st);
+cudaError_t launch_push_round(const GraphDev& g, const BatchDev& b, int cur, uint64_t nf,
+                              uint64_t nh, uint32_t round, int num_sms, cudaStream_t st);
+
+// walk.cu
+cudaError_t launch_residuals(const GraphDev& g, const BatchDev& b, cudaStream_t st);
+cudaError_t launch_walks(const GraphDev& g, const BatchDev& b, int num_sms, cudaStream_t st);
+cudaError_t launch_philox_table(const uint32_t* ctr_key, uint32_t* out, int count,
+                                cudaStream_t st);
+
+// topk.cu
+cudaError_t launch_estimate(const double* res, const unsigned long long* acc, double* est,
+                            uint64_t count, int num_sms, cudaStream_t st);
+// Scratch of the top-k select: hist [nrows][kBins], slots [nrows], cand [nrows][kSortCap].
+struct TopkScratch {
+  uint32_t* hist;
+  TopkSlot* slots;
+  unsigned long long* cand_key;  // estimate bits
+  uint32_t* cand_id;
+};
+size_t topk_scratch_bytes(int nrows);
+TopkScratch topk_scratch_carve(void* base, int nrows);
+cudaError_t launch_topk(const double* est, int64_t n, int nrows, uint32_t k, int32_t* out_ids,
+                        double* out_vals, const TopkScratch& s, int num_sms, cudaStream_t st);
+
+}  // namespace fora

@@ -1,0 +1,311 @@
+// Walk phase of Alg. 2 over a batch of sources.
+//
+//   k_residual_count / k_residual_scan / k_residual_emit:
+//     R = {(slot, v) : r(v) > 0} in ascending (slot, v); omega_v = ceil(r(v) * C) with
+//     C = omega / r_sum (Alg. 2 line 3); exclusive offsets of omega_v over R (one flat
+//     walk index space for all sources) and the fixed-point weight
+//     W_v = rint(r(v)/omega_v * 2^63) of every walk from v (Alg. 2 line 7: a_v r_sum/omega).
+//   k_walks:
+//     walk g in [0, W) belongs to the entry i with offset[i] <= g < offset[i+1] and is
+//     walk j = g - offset[i] of node v; it reads its own Philox4x32-10 stream with
+//     counter (c, j, v, s) and stops with probability alpha at every node
+//     (Section 2.1); count[end] += 1 and acc[end] += W_v.
+// Each warp owns a contiguous range of walk indices (lanes interleaved by 32), so a
+// warp locates its first entry once and then advances through R monotonically.
+#include "fora_engine.cuh"
+
+namespace fora {
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kResidualThreads = 256;
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// The word stream of one walk: blocks c = 0, 1, ... of Philox with counter (c, j, v, s).
+struct WalkStream {
+  uint32_t c, j, v, s;
+  uint2 key;
+  uint32_t w0, w1, w2, w3;
+  int avail;
+  __device__ __forceinline__ uint32_t next() {
+    if (avail == 0) {
+      const uint4 o = philox4x32_10(make_uint4(c, j, v, s), key);
+      ++c;
+      w0 = o.x; w1 = o.y; w2 = o.z; w3 = o.w;
+      avail = 4;
+    }
+    const uint32_t r = w0;
+    w0 = w1; w1 = w2; w2 = w3;
+    --avail;
+    return r;
+  }
+};
+
+// omega_v = ceil(r * C); W_v = rint((r / omega_v) * 2^63)
+__device__ __forceinline__ double walks_of(double r, double C) { return ceil(__dmul_rn(r, C)); }
+__device__ __forceinline__ unsigned long long weight_of(double r, double omega) {
+  return __double2ull_rn(__dmul_rn(__ddiv_rn(r, omega), 0x1p63));
+}
+
+// Contiguous element range of block `blk` out of `nblk` over [0, total).
+__device__ __forceinline__ void block_range(unsigned long long total, int blk, int nblk,
+                                            unsigned long long* beg, unsigned long long* end) {
+  *beg = total * (unsigned long long)blk / (unsigned long long)nblk;
+  *end = total * (unsigned long long)(blk + 1) / (unsigned long long)nblk;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T x) {
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const T t = __shfl_up_sync(kFull, x, off);
+    if ((int)(threadIdx.x & 31) >= off) x += t;
+  }
+  return x;
+}
+
+// Block-wide exclusive scan of (count, walks) pairs; also returns the block totals.
+// Every thread of the block must call it.
+__device__ __forceinline__ void block_excl_scan2(unsigned long long c, unsigned long long w,
+                                                 unsigned long long* ce, unsigned long long* we,
+                                                 unsigned long long* ct, unsigned long long* wt) {
+  __shared__ unsigned long long sc[32], sw[32];
+  __shared__ unsigned long long tc, tw;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned long long ci = warp_incl_scan(c), wi = warp_incl_scan(w);
+  if (lane == 31) { sc[wid] = ci; sw[wid] = wi; }
+  __syncthreads();
+  if (wid == 0) {
+    const unsigned long long a = lane < nw ? sc[lane] : 0, bb = lane < nw ? sw[lane] : 0;
+    const unsigned long long ai = warp_incl_scan(a), bi = warp_incl_scan(bb);
+    if (lane < nw) { sc[lane] = ai - a; sw[lane] = bi - bb; }
+    if (lane == 31) { tc = ai; tw = bi; }
+  }
+  __syncthreads();
+  *ce = sc[wid] + ci - c;
+  *we = sw[wid] + wi - w;
+  *ct = tc;
+  *wt = tw;
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kResidualThreads) k_residual_count(GraphDev g, BatchDev b) {
+  const unsigned long long total = (unsigned long long)b.nsrc * (unsigned long long)g.n;
+  unsigned long long beg, end;
+  block_range(total, blockIdx.x, gridDim.x, &beg, &end);
+  unsigned long long cnt = 0, walks = 0;
+  // per-source sums, flushed whenever this thread's elements move to another source
+  unsigned long long i = beg + threadIdx.x;
+  uint32_t slot = (uint32_t)(i / (unsigned long long)g.n);
+  unsigned long long slot_end = (unsigned long long)(slot + 1) * (unsigned long long)g.n;
+  unsigned long long s_cnt = 0, s_walks = 0;
+  double s_sum = 0.0;
+  for (; i < end; i += kResidualThreads) {
+    while (i >= slot_end) {
+      if (s_cnt) {
+        atomicAdd(&b.stats[slot].residual_nodes, s_cnt);
+        atomicAdd(&b.stats[slot].walks, s_walks);
+        atomicAdd(&b.stats[slot].rsum, s_sum);
+      }
+      s_cnt = 0; s_walks = 0; s_sum = 0.0;
+      ++slot;
+      slot_end += (unsigned long long)g.n;
+    }
+    const double r = b.r[i];
+    if (r > 0.0) {
+      const unsigned long long w = (unsigned long long)walks_of(r, b.walk_scale);
+      ++cnt; walks += w;
+      ++s_cnt; s_walks += w; s_sum += r;
+    }
+  }
+  if (s_cnt && slot < (uint32_t)b.nsrc) {
+    atomicAdd(&b.stats[slot].residual_nodes, s_cnt);
+    atomicAdd(&b.stats[slot].walks, s_walks);
+    atomicAdd(&b.stats[slot].rsum, s_sum);
+  }
+  unsigned long long ce, we, ct, wt;
+  block_excl_scan2(cnt, walks, &ce, &we, &ct, &wt);
+  if (threadIdx.x == 0) {
+    b.blk_cnt[blockIdx.x] = ct;
+    b.blk_walks[blockIdx.x] = wt;
+  }
+}
+
+// One block: exclusive scan of the per-block totals; totals; per-source walk limit.
+__global__ void __launch_bounds__(1024) k_residual_scan(BatchDev b) {
+  __shared__ unsigned long long carry_c, carry_w;
+  if (threadIdx.x == 0) { carry_c = 0; carry_w = 0; }
+  __syncthreads();
+  for (int base = 0; base < b.residual_grid; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const unsigned long long c = i < b.residual_grid ? b.blk_cnt[i] : 0;
+    const unsigned long long w = i < b.residual_grid ? b.blk_walks[i] : 0;
+    unsigned long long ce, we, ct, wt;
+    block_excl_scan2(c, w, &ce, &we, &ct, &wt);
+    if (i < b.residual_grid) {
+      b.blk_cnt[i] = carry_c + ce;
+      b.blk_walks[i] = carry_w + we;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) { carry_c += ct; carry_w += wt; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    b.totals[0] = carry_c;
+    b.totals[1] = carry_w;
+    b.wr_offset[carry_c] = carry_w;
+  }
+  for (int s = threadIdx.x; s < b.nsrc; s += blockDim.x)
+    if (b.stats[s].walks > 0xFFFFFFFFull) atomicOr(b.err, kErrWalkOverflow);
+}
+
+__global__ void __launch_bounds__(kResidualThreads) k_residual_emit(GraphDev g, BatchDev b) {
+  const unsigned long long total = (unsigned long long)b.nsrc * (unsigned long long)g.n;
+  unsigned long long beg, end;
+  block_range(total, blockIdx.x, gridDim.x, &beg, &end);
+  unsigned long long pos = b.blk_cnt[blockIdx.x];
+  unsigned long long woff = b.blk_walks[blockIdx.x];
+  for (unsigned long long tile = beg; tile < end; tile += kResidualThreads) {
+    const unsigned long long i = tile + threadIdx.x;
+    const double r = i < end ? b.r[i] : 0.0;
+    const bool live = r > 0.0;
+    const double omega = live ? walks_of(r, b.walk_scale) : 0.0;
+    unsigned long long ce, we, ct, wt;
+    block_excl_scan2(live ? 1ull : 0ull, (unsigned long long)omega, &ce, &we, &ct, &wt);
+    if (live) {
+      const unsigned long long slot = i / (unsigned long long)g.n;
+      const unsigned long long v = i - slot * (unsigned long long)g.n;
+      b.wr_entry[pos + ce] = (slot << 32) | v;
+      b.wr_offset[pos + ce] = woff + we;
+      b.wr_weight[pos + ce] = weight_of(r, omega);
+    }
+    pos += ct;
+    woff += wt;
+  }
+}
+
+// Largest i in [lo, hi) with off[i] <= g (off non-decreasing, off[lo] <= g).
+__device__ __forceinline__ unsigned long long find_entry(const unsigned long long* off,
+                                                         unsigned long long lo,
+                                                         unsigned long long hi,
+                                                         unsigned long long g) {
+  while (hi - lo > 1) {
+    const unsigned long long mid = lo + ((hi - lo) >> 1);
+    if (off[mid] <= g) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256) k_walks(GraphDev g, BatchDev b) {
+  if (*b.err) return;
+  const unsigned long long W = b.totals[1];
+  const unsigned long long nR = b.totals[0];
+  if (W == 0) return;
+  const uint32_t lane = threadIdx.x & 31;
+  const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  const unsigned long long wbeg = W * warp / nwarps, wend = W * (warp + 1) / nwarps;
+  unsigned long long gidx = wbeg + lane;
+  const unsigned long long* off = b.wr_offset;
+  unsigned long long idx = gidx < wend ? find_entry(off, 0, nR, gidx) : 0;
+  unsigned long long steps_here = 0;  // moves of this lane's walks of source `cur_slot`
+  uint32_t cur_slot = 0xFFFFFFFFu;
+  const uint2 key = make_uint2((uint32_t)b.seed, (uint32_t)(b.seed >> 32));
+  const uint32_t t_alpha = b.alpha_threshold;
+  bool capped = false;
+  for (; gidx < wend; gidx += 32) {
+    while (off[idx + 1] <= gidx) ++idx;
+    const unsigned long long entry = b.wr_entry[idx];
+    const uint32_t slot = (uint32_t)(entry >> 32), v = (uint32_t)entry;
+    if (slot != cur_slot) {  // a lane's walks visit sources in ascending order
+      if (steps_here) atomicAdd(&b.stats[cur_slot].walk_steps, steps_here);
+      steps_here = 0;
+      cur_slot = slot;
+    }
+    WalkStream rng;
+    rng.c = 0;
+    rng.j = (uint32_t)(gidx - off[idx]);
+    rng.v = v;
+    rng.s = (uint32_t)b.sources[slot];
+    rng.key = key;
+    rng.avail = 0;
+    uint32_t x = v;
+    uint32_t steps = 0;
+    bool stopped = false;
+    for (; steps < 16384u; ++steps) {
+      if (rng.next() < t_alpha) { stopped = true; break; }
+      const uint32_t rb = g.row[x];
+      const uint32_t d = g.row[x + 1] - rb;
+      unsigned long long m = (unsigned long long)rng.next() * d;
+      uint32_t low = (uint32_t)m;
+      if (low < d) {
+        const uint32_t reject_below = (0u - d) % d;
+        // each retry happens with probability < d / 2^32; 64 in a row never occur in practice
+        for (int tries = 0; low < reject_below && tries < 64; ++tries) {
+          m = (unsigned long long)rng.next() * d;
+          low = (uint32_t)m;
+        }
+        if (low < reject_below) break;  // reported as a capped walk
+      }
+      x = (uint32_t)g.col[rb + (uint32_t)(m >> 32)];
+    }
+    if (!stopped) { capped = true; break; }
+    steps_here += steps;
+    const unsigned long long gi = (unsigned long long)slot * (unsigned long long)g.n + x;
+    atomicAdd(&b.cnt[gi], 1u);
+    atomicAdd(&b.acc[gi], b.wr_weight[idx]);
+  }
+  if (capped) atomicOr(b.err, kErrWalkCap);
+  if (steps_here) atomicAdd(&b.stats[cur_slot].walk_steps, steps_here);
+}
+
+__global__ void k_philox_table(const uint32_t* ck, uint32_t* out, int count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const uint4 o = philox4x32_10(make_uint4(ck[6 * i], ck[6 * i + 1], ck[6 * i + 2], ck[6 * i + 3]),
+                                make_uint2(ck[6 * i + 4], ck[6 * i + 5]));
+  out[4 * i] = o.x; out[4 * i + 1] = o.y; out[4 * i + 2] = o.z; out[4 * i + 3] = o.w;
+}
+
+}  // namespace
+
+cudaError_t launch_residuals(const GraphDev& g, const BatchDev& b, cudaStream_t st) {
+  k_residual_count<<<b.residual_grid, kResidualThreads, 0, st>>>(g, b);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_residual_scan<<<1, 1024, 0, st>>>(b);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_residual_emit<<<b.residual_grid, kResidualThreads, 0, st>>>(g, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_walks(const GraphDev& g, const BatchDev& b, int num_sms, cudaStream_t st) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walks, 256, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  k_walks<<<num_sms * per_sm, 256, 0, st>>>(g, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox_table(const uint32_t* ctr_key, uint32_t* out, int count,
+                                cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  k_philox_table<<<(count + 127) / 128, 128, 0, st>>>(ctr_key, out, count);
+  return cudaGetLastError();
+}
+
+}  // namespace fora

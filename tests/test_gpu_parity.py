@@ -1,0 +1,246 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI (needs a GPU).
+
+Tolerances: reserves and residues of the push within 1e-12 absolute (FP64 atomics
+reorder the sums); walk counts, fixed-point walk weights, estimates and top-k
+bit-exact when both sides run the walk phase on the oracle's reserve and residue.
+"""
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+from oracle import exact
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1908_10583_gb300 as fora  # noqa: E402
+from paper_1908_10583_gb300 import build as fbuild  # noqa: E402
+
+ATOL_PUSH = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    fbuild.build()
+    fora.load()
+
+
+def cuda_zeros(shape, dtype):
+    return torch.zeros(shape, dtype=dtype, device="cuda")
+
+
+def run_debug(g, sources, params, given=None):
+    """Batched query with all intermediate arrays; given = (reserve, residue) numpy [S, n]."""
+    S, n = len(sources), g.n
+    dbg = dict(reserve=cuda_zeros((S, n), torch.float64), residue=cuda_zeros((S, n), torch.float64),
+               count=cuda_zeros((S, n), torch.int32), acc=cuda_zeros((S, n), torch.int64),
+               estimate=cuda_zeros((S, n), torch.float64))
+    if given is not None:
+        dbg["reserve"].copy_(torch.from_numpy(np.ascontiguousarray(given[0])))
+        dbg["residue"].copy_(torch.from_numpy(np.ascontiguousarray(given[1])))
+    ids, vals, st = g.ssppr_batch_debug(sources, params, dbg, given_push=given is not None)
+    torch.cuda.synchronize()
+    out = {k: v.cpu().numpy() for k, v in dbg.items()}
+    out["count"] = out["count"].view(np.uint32)
+    out["acc"] = out["acc"].view(np.uint64)
+    return ids, vals, st, out
+
+
+@pytest.fixture(scope="module")
+def rmat14():
+    rp, col = inputs.rmat_csr(14, 8, 1)
+    return rp, col, fora.Graph(rp, col)
+
+
+def test_device_philox_matches_oracle_and_published_vectors():
+    rng = np.random.default_rng(0)
+    rows = rng.integers(0, 2**32, size=(500, 6), dtype=np.uint64).astype(np.uint32)
+    kat = np.array([[0, 0, 0, 0, 0, 0], [0xffffffff] * 6,
+                    [0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344, 0xa4093822, 0x299f31d0]],
+                   dtype=np.uint32)
+    rows = np.vstack([kat, rows])
+    dev = fora.philox(rows)
+    for r, d in zip(rows, dev):
+        np.testing.assert_array_equal(d, oracle.philox4x32_10(r[:4], r[4:]))
+    np.testing.assert_array_equal(dev[0], [0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8])
+
+
+def test_resolved_parameters_are_bit_identical_to_the_oracle(rmat14):
+    rp, col, g = rmat14
+    n = len(rp) - 1
+    for eps in (0.5, 0.3, 0.1):
+        p = fora.Params.make(eps=eps)
+        rmax, C, t = g.resolve(p)
+        assert rmax == oracle.rmax_rule(eps, 1.0 / n, 1.0 / n, rp[-1])
+        assert C == oracle.walk_scale(eps, 1.0 / n, 1.0 / n)
+        assert t == oracle.alpha_threshold(0.2)
+
+
+def test_push_matches_oracle(rmat14):
+    rp, col, g = rmat14
+    n = len(rp) - 1
+    sources = inputs.uniform_sources(n, 10, inputs.SOURCE_SEED)
+    p = fora.Params.make(k=50)
+    ids, vals, st, out = run_debug(g, sources, p)
+    rmax = g.resolve(p)[0]
+    for i, s in enumerate(sources):
+        res, r, pst = oracle.forward_push(rp, col, s, 0.2, rmax)
+        np.testing.assert_allclose(out["reserve"][i], res, rtol=0, atol=ATOL_PUSH)
+        np.testing.assert_allclose(out["residue"][i], r, rtol=0, atol=ATOL_PUSH)
+        # the same nodes were pushed: the frontiers agreed round by round
+        assert st[i].pushes == pst.pushes and st[i].edge_pushes == pst.edge_pushes
+        assert st[i].push_rounds == pst.rounds
+        assert st[i].rsum == pytest.approx(pst.rsum, abs=1e-12)
+
+
+def test_walks_and_topk_bit_exact_on_oracle_residues(rmat14):
+    rp, col, g = rmat14
+    n = len(rp) - 1
+    sources = inputs.uniform_sources(n, 10, inputs.SOURCE_SEED)
+    p = fora.Params.make(k=50, seed=inputs.WALK_SEED)
+    qs = [oracle.ssppr(rp, col, s, k=50, seed=inputs.WALK_SEED) for s in sources]
+    given = (np.stack([q.reserve for q in qs]), np.stack([q.residue for q in qs]))
+    ids, vals, st, out = run_debug(g, sources, p, given=given)
+    for i, q in enumerate(qs):
+        np.testing.assert_array_equal(out["count"][i], q.count)
+        np.testing.assert_array_equal(out["acc"][i], q.acc)
+        np.testing.assert_array_equal(out["estimate"][i], q.est)
+        np.testing.assert_array_equal(ids[i], q.ids)
+        np.testing.assert_array_equal(vals[i], q.vals)
+        assert st[i].walks == q.walk.walks
+        assert st[i].walk_steps == q.walk.walk_steps
+        assert st[i].residual_nodes == q.walk.residual_nodes
+
+
+def test_full_query_matches_oracle(rmat14):
+    """Without injected residues: same counts (omega_v = ceil(r C) is insensitive to
+    the last bits of r), estimates within the push tolerance, same top-k up to near-ties."""
+    rp, col, g = rmat14
+    n = len(rp) - 1
+    sources = inputs.uniform_sources(n, 10, inputs.SOURCE_SEED)
+    p = fora.Params.make(k=50, seed=inputs.WALK_SEED)
+    ids, vals, st, out = run_debug(g, sources, p)
+    for i, s in enumerate(sources):
+        q = oracle.ssppr(rp, col, s, k=50, seed=inputs.WALK_SEED)
+        np.testing.assert_array_equal(out["count"][i], q.count)
+        np.testing.assert_allclose(out["estimate"][i], q.est, rtol=0, atol=ATOL_PUSH)
+        np.testing.assert_allclose(vals[i], q.est[ids[i]], rtol=0, atol=ATOL_PUSH)
+        kth = q.vals[-1]
+        sure = set(np.flatnonzero(q.est > kth + 2 * ATOL_PUSH).tolist())
+        assert sure <= set(ids[i].tolist())
+        assert np.all(q.est[ids[i]] >= kth - 2 * ATOL_PUSH)
+
+
+def test_single_and_batch_agree(rmat14):
+    rp, col, g = rmat14
+    n = len(rp) - 1
+    sources = inputs.uniform_sources(n, 6, 7)
+    p = fora.Params.make(k=50, seed=11)
+    ids_b, vals_b, st_b, out_b = run_debug(g, sources, p)
+    given = (out_b["reserve"], out_b["residue"])
+    # the same residues, one source at a time: bit-exact walk phase and top-k
+    for i, s in enumerate(sources):
+        ids1, vals1, _, out1 = run_debug(g, [s], p, given=(given[0][i:i + 1], given[1][i:i + 1]))
+        np.testing.assert_array_equal(out1["count"][0], out_b["count"][i])
+        np.testing.assert_array_equal(out1["acc"][0], out_b["acc"][i])
+        np.testing.assert_array_equal(ids1[0], ids_b[i])
+        # and the public single-source entry point agrees up to the push rounding
+        ids2, vals2, st2 = g.ssppr(s, p)
+        np.testing.assert_allclose(vals2, vals_b[i], rtol=0, atol=ATOL_PUSH)
+        assert st2.walks == st_b[i].walks
+
+
+def test_eps_accuracy_against_power_iteration(rmat14):
+    """Def. 1 / Lemma (layerppr-conc): relative error <= eps for every t with pi >= delta."""
+    rp, col, g = rmat14
+    n = len(rp) - 1
+    sources = inputs.uniform_sources(n, 10, inputs.SOURCE_SEED)
+    truth = exact.power_iteration(rp, col, 0.2, sources)
+    p = fora.Params.make(k=50, eps=0.5)
+    _, _, _, out = run_debug(g, sources, p)
+    fails = 0
+    for i in range(len(sources)):
+        big = truth[i] >= 1.0 / n
+        rel = np.abs(out["estimate"][i][big] - truth[i][big]) / truth[i][big]
+        fails += int(rel.max() > 0.5)
+    assert fails == 0
+
+
+def test_hub_source_and_mc_mode(rmat14):
+    """The largest-degree node as source (chunked hub pushes) and r_max = 1 (no push,
+    pure Monte-Carlo), both against the oracle on the same residues."""
+    rp, col, g = rmat14
+    deg = np.diff(rp)
+    hub = int(np.argmax(deg))
+    assert deg[hub] > 256
+    for rmax in (0.0, 1.0):
+        p = fora.Params.make(k=20, rmax=rmax, seed=3)
+        q = oracle.ssppr(rp, col, hub, k=20, rmax=rmax, seed=3)
+        ids, vals, st, out = run_debug(g, [hub], p)
+        np.testing.assert_allclose(out["reserve"][0], q.reserve, rtol=0, atol=ATOL_PUSH)
+        np.testing.assert_array_equal(out["count"][0], q.count)
+        np.testing.assert_array_equal(ids[0], q.ids)
+        assert st[0].push_rounds == q.push.rounds
+
+
+def test_tiny_graphs_and_ragged_sizes():
+    # hand-worked triangle (round-synchronous push), see the oracle pins
+    rp, col = inputs.csr_from_edges(3, [(0, 1), (0, 2), (1, 2), (2, 0)])
+    g = fora.Graph(rp, col)
+    p = fora.Params.make(alpha=0.5, rmax=0.1, k=3, delta=0.5, pf=0.5)
+    ids, vals, st, out = run_debug(g, [0], p)
+    np.testing.assert_array_equal(out["reserve"][0], [0.5, 0.125, 0.1875])
+    np.testing.assert_array_equal(out["residue"][0], [0.1875, 0.0, 0.0])
+    assert st[0].push_rounds == 3
+    q = oracle.ssppr(rp, col, 0, alpha=0.5, rmax=0.1, k=3, delta=0.5, pf=0.5)
+    np.testing.assert_array_equal(out["count"][0], q.count)
+    np.testing.assert_array_equal(ids[0], q.ids)
+    # one node with a self-loop; k = n
+    g1 = fora.Graph(np.array([0, 1]), np.array([0], dtype=np.int32))
+    ids, vals, _ = g1.ssppr(0, fora.Params.make(k=1, delta=0.5, pf=0.5))
+    assert ids[0] == 0 and vals[0] == pytest.approx(1.0, abs=1e-12)
+    # a ragged random graph (n not a power of two), k = n, several sources
+    rng = np.random.default_rng(5)
+    n = 1013
+    edges = [(v, int(u)) for v in range(n) for u in rng.integers(0, n, size=1 + rng.poisson(3))]
+    rp, col = inputs.csr_from_edges(n, edges)
+    g2 = fora.Graph(rp, col)
+    src = [0, 1012, 500]
+    p = fora.Params.make(k=n, seed=9)
+    ids, vals, st, out = run_debug(g2, src, p)
+    for i, s in enumerate(src):
+        q = oracle.ssppr(rp, col, s, k=n, seed=9)
+        np.testing.assert_allclose(out["reserve"][i], q.reserve, rtol=0, atol=ATOL_PUSH)
+        np.testing.assert_array_equal(out["count"][i], q.count)
+        assert sorted(ids[i].tolist()) == list(range(n))
+
+
+@pytest.mark.parametrize("n,nrows,k", [(1, 1, 1), (1000, 3, 1000), (5000, 4, 500),
+                                       (300_000, 2, 4096), (2**20, 1, 500)])
+def test_standalone_topk_bit_exact(n, nrows, k):
+    rng = np.random.default_rng(n)
+    est = rng.integers(0, 50, size=(nrows, n)) / 64.0  # heavy ties
+    est[:, :: 7] = rng.random((nrows, len(range(0, n, 7))))
+    ids, vals = fora.topk(torch.from_numpy(est).cuda(), k)
+    ids, vals = ids.cpu().numpy(), vals.cpu().numpy()
+    for r in range(nrows):
+        order = np.lexsort((np.arange(n), -est[r]))[:k]
+        np.testing.assert_array_equal(ids[r], order)
+        np.testing.assert_array_equal(vals[r], est[r][order])
+
+
+def test_errors_are_reported(rmat14):
+    rp, col, g = rmat14
+    with pytest.raises(fora.FORAError) as e:
+        g.ssppr(len(rp), fora.Params.make())
+    assert e.value.code == fora.FORA_ERR_BAD_ARG
+    with pytest.raises(fora.FORAError):
+        g.ssppr(0, fora.Params.make(alpha=1.0))
+    with pytest.raises(fora.FORAError):
+        g.ssppr(0, fora.Params.make(k=5000))
+    # the graph stays usable after a rejected call
+    ids, vals, st = g.ssppr(0, fora.Params.make(k=5))
+    assert len(ids) == 5

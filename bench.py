@@ -46,6 +46,7 @@ def parse_args():
     ap.add_argument("--cpu-sources", type=int, default=8,
                     help="sources in the bounded CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--stats", action="store_true", help="per-step counters to stderr")
     return ap.parse_args()
 
 
@@ -240,7 +241,7 @@ def run_fora(args):
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
         rounds = max(s.push_rounds for s in st)
-        launches += 2 * rounds + 1 + 3 + 1 + 1 + 19
+        launches += 4 + 4 * rounds + 3 + 1 + 1 + 19  # push, residuals, walks, estimate, top-k
         for key in phase:
             phase[key] += getattr(st[0], key)
         walk_ms.append(st[0].ms_walk)
@@ -251,6 +252,13 @@ def run_fora(args):
         steps_total += ns
         walk_bytes.append(WALK_BYTES_PER_MOVE * ns + WALK_BYTES_PER_WALK * nw +
                           WALK_BYTES_PER_ENTRY * nr)
+        if args.stats:
+            print(json.dumps({"step": step, "ms": step_ms[-1], "rounds": rounds,
+                              "pushes": sum(s.pushes for s in st),
+                              "edge_pushes": sum(s.edge_pushes for s in st),
+                              "residual_nodes": nr, "walks": nw, "moves": ns,
+                              "rsum_mean": sum(s.rsum for s in st) / len(st),
+                              **{k_: getattr(st[0], k_) for k_ in phase}}), file=sys.stderr)
     torch.cuda.synchronize()
     clk = clocks.stop()
     total_ms = sum(step_ms)

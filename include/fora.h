@@ -137,7 +137,7 @@ int fora_ssppr(fora_graph *g, const fora_params *params, int32_t source, int32_t
  * sources: HOST array of nsrc ids.  out_ids / out_vals: [nsrc][k] row-major.
  * stats: NULL or [nsrc].  Every source gives bit for bit the walk counts and
  * top-k it would give alone (same Philox counters), up to the FP64 rounding
- * order of the push.  The workspace for nsrc sources (about 52 bytes per
+ * order of the push.  The workspace for nsrc sources (about 56 bytes per
  * source and node) is allocated on the first call that needs it and kept.
  */
 int fora_ssppr_batch(fora_graph *g, const fora_params *params, const int32_t *sources,

@@ -59,12 +59,13 @@ struct fora_graph {
   int cap = 0;
   double* r = nullptr;
   double* res = nullptr;
-  uint32_t* cnt = nullptr;
-  unsigned long long* acc = nullptr;
+  Tally* tally = nullptr;
   unsigned long long* q[2] = {nullptr, nullptr};
   unsigned long long* hub[2] = {nullptr, nullptr};
   double* fa = nullptr;
   unsigned long long* small = nullptr;  // counters[4] totals[2]
+  uint32_t* mask = nullptr;
+  uint32_t* active = nullptr;
   uint32_t* err = nullptr;
   int32_t* sources = nullptr;
   double* rmax = nullptr;
@@ -83,9 +84,9 @@ struct fora_graph {
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 
   void release_workspace() {
-    dfree(r); dfree(res); dfree(cnt); dfree(acc);
+    dfree(r); dfree(res); dfree(tally);
     dfree(q[0]); dfree(q[1]); dfree(hub[0]); dfree(hub[1]); dfree(fa);
-    dfree(small); dfree(err); dfree(sources); dfree(rmax); dfree(stats); dfree(blk);
+    dfree(small); dfree(mask); dfree(active); dfree(err); dfree(sources); dfree(rmax); dfree(stats); dfree(blk);
     if (topk_scratch) cudaFree(topk_scratch);
     topk_scratch = nullptr;
     dfree(out_ids); dfree(out_vals);
@@ -109,14 +110,15 @@ int ensure_workspace(fora_graph* g, int nsrc) {
   g->residual_grid = g->num_sms * 8;
   CUDA_TRY(cudaMalloc(&g->r, N * sizeof(double)));
   CUDA_TRY(cudaMalloc(&g->res, N * sizeof(double)));
-  CUDA_TRY(cudaMalloc(&g->cnt, N * sizeof(uint32_t)));
-  CUDA_TRY(cudaMalloc(&g->acc, N * sizeof(unsigned long long)));
+  CUDA_TRY(cudaMalloc(&g->tally, N * sizeof(Tally)));
   CUDA_TRY(cudaMalloc(&g->q[0], (N + 1) * sizeof(unsigned long long)));
   CUDA_TRY(cudaMalloc(&g->q[1], (N + 1) * sizeof(unsigned long long)));
   CUDA_TRY(cudaMalloc(&g->fa, (N + 1) * sizeof(double)));
   CUDA_TRY(cudaMalloc(&g->hub[0], H * sizeof(unsigned long long)));
   CUDA_TRY(cudaMalloc(&g->hub[1], H * sizeof(unsigned long long)));
   CUDA_TRY(cudaMalloc(&g->small, 8 * sizeof(unsigned long long)));
+  CUDA_TRY(cudaMalloc(&g->mask, (size_t)nsrc * (((size_t)g->n + 31) / 32) * sizeof(uint32_t)));
+  CUDA_TRY(cudaMalloc(&g->active, 2 * (size_t)nsrc * sizeof(uint32_t)));
   CUDA_TRY(cudaMalloc(&g->err, sizeof(uint32_t)));
   CUDA_TRY(cudaMalloc(&g->sources, nsrc * sizeof(int32_t)));
   CUDA_TRY(cudaMalloc(&g->rmax, nsrc * sizeof(double)));
@@ -198,8 +200,7 @@ int run_batch(fora_graph* g, const fora_params* p, const int32_t* sources, int n
   }
   CUDA_TRY(cudaMemcpyAsync(g->sources, g->h_sources, nsrc * sizeof(int32_t), cudaMemcpyHostToDevice, stream));
   CUDA_TRY(cudaMemcpyAsync(g->rmax, g->h_rmax, nsrc * sizeof(double), cudaMemcpyHostToDevice, stream));
-  CUDA_TRY(cudaMemsetAsync(g->cnt, 0, N * sizeof(uint32_t), stream));
-  CUDA_TRY(cudaMemsetAsync(g->acc, 0, N * sizeof(unsigned long long), stream));
+  CUDA_TRY(cudaMemsetAsync(g->tally, 0, N * sizeof(Tally), stream));
   CUDA_TRY(cudaMemsetAsync(g->small, 0, 8 * sizeof(unsigned long long), stream));
   CUDA_TRY(cudaMemsetAsync(g->err, 0, sizeof(uint32_t), stream));
   CUDA_TRY(cudaMemsetAsync(g->stats, 0, nsrc * sizeof(SlotStats), stream));
@@ -211,10 +212,12 @@ int run_batch(fora_graph* g, const fora_params* p, const int32_t* sources, int n
   b.walk_scale = rp.walk_scale;
   b.alpha_threshold = rp.alpha_threshold;
   b.seed = p->seed;
-  b.r = g->r; b.res = g->res; b.cnt = g->cnt; b.acc = g->acc;
+  b.r = g->r; b.res = g->res; b.tally = g->tally;
   b.q[0] = g->q[0]; b.q[1] = g->q[1]; b.fa = g->fa;
   b.hub[0] = g->hub[0]; b.hub[1] = g->hub[1];
   b.counters = g->small;
+  b.mask = g->mask;
+  b.active = g->active;
   b.totals = g->small + 4;
   b.sources = g->sources; b.rmax = g->rmax; b.stats = g->stats; b.err = g->err;
   b.wr_entry = g->q[0];
@@ -262,13 +265,12 @@ int run_batch(fora_graph* g, const fora_params* p, const int32_t* sources, int n
   if (timed) CUDA_TRY(cudaEventRecord(g->ev[2], stream));
   CUDA_TRY(launch_walks(gd, b, g->num_sms, stream));
   if (timed) CUDA_TRY(cudaEventRecord(g->ev[3], stream));
-  if (dbg && dbg->count)
-    CUDA_TRY(cudaMemcpyAsync(dbg->count, g->cnt, N * sizeof(uint32_t), cudaMemcpyDeviceToDevice, stream));
-  if (dbg && dbg->acc)
-    CUDA_TRY(cudaMemcpyAsync(dbg->acc, g->acc, N * sizeof(uint64_t), cudaMemcpyDeviceToDevice, stream));
+  if (dbg && (dbg->count || dbg->acc))
+    CUDA_TRY(launch_unpack_tally(g->tally, dbg->count, reinterpret_cast<unsigned long long*>(dbg->acc), N,
+                                 g->num_sms, stream));
 
   // ---- estimate and top-k (the residue array becomes the estimate) ----
-  CUDA_TRY(launch_estimate(g->res, g->acc, g->r, N, g->num_sms, stream));
+  CUDA_TRY(launch_estimate(g->res, g->tally, g->r, N, g->num_sms, stream));
   if (dbg && dbg->estimate)
     CUDA_TRY(cudaMemcpyAsync(dbg->estimate, g->r, N * sizeof(double), cudaMemcpyDeviceToDevice, stream));
   int32_t* ids_dev = out_dev ? out_ids : g->out_ids;

@@ -29,6 +29,14 @@ struct GraphDev {
   const int32_t* col;   // [m]
 };
 
+// Walk end tally of one (source, node): fixed-point weight and count share one
+// 16-byte record, so a walk's end touches a single L2 sector.
+struct __align__(16) Tally {
+  unsigned long long acc;  // sum of walk weights, 2^-63 units
+  uint32_t cnt;            // number of walks
+  uint32_t pad;
+};
+
 // Per-source counters kept on the device during a call.
 struct SlotStats {
   unsigned long long pushes;
@@ -61,12 +69,13 @@ struct BatchDev {
   uint64_t seed;
   double* r;                 // residue, later the estimate
   double* res;               // reserve
-  uint32_t* cnt;             // walk end counts
-  unsigned long long* acc;   // fixed-point walk weight (2^-63 units)
+  Tally* tally;              // walk ends per (source, node)
   unsigned long long* q[2];  // frontier queues: (slot << 32) | v
   double* fa;                // per frontier entry: (1 - alpha) r(v) / d(v)
   unsigned long long* hub[2];  // hub chunk items
   unsigned long long* counters;  // [4]: frontier/hub counts of parity 0 and 1
+  uint32_t* mask;            // crossing mask, one bit per (slot, node), rows padded to words
+  uint32_t* active;          // [2][nsrc]: sources with entries in q[0] / q[1]
   const int32_t* sources;    // [nsrc]
   const double* rmax;        // [nsrc]
   SlotStats* stats;          // [nsrc]
@@ -75,26 +84,30 @@ struct BatchDev {
   unsigned long long* wr_entry;   // residual list: (slot << 32) | v   (aliases q[0])
   unsigned long long* wr_offset;  // exclusive walk offsets, [|R| + 1]  (aliases q[1])
   unsigned long long* wr_weight;  // fixed-point weight per walk        (aliases fa)
-  unsigned long long* blk_cnt;    // [grid] residual nodes per block, then block offsets
-  unsigned long long* blk_walks;  // [grid] walks per block, then block offsets
+  unsigned long long* blk_cnt;    // [grid] per-block counts, then block offsets
+  unsigned long long* blk_walks;  // [grid] per-block counts, then block offsets
   unsigned long long* totals;     // [2]: |R|, W
   int residual_grid;
 };
 
 // push.cu
 cudaError_t launch_push_init(const GraphDev& g, const BatchDev& b, cudaStream_t st);
+cudaError_t launch_push_detect(const GraphDev& g, const BatchDev& b, int par, uint32_t round,
+                               cudaStream_t st);
 cudaError_t launch_push_round(const GraphDev& g, const BatchDev& b, int cur, uint64_t nf,
                               uint64_t nh, uint32_t round, int num_sms, cudaStream_t st);
 
 // walk.cu
 cudaError_t launch_residuals(const GraphDev& g, const BatchDev& b, cudaStream_t st);
 cudaError_t launch_walks(const GraphDev& g, const BatchDev& b, int num_sms, cudaStream_t st);
+cudaError_t launch_unpack_tally(const Tally* t, uint32_t* cnt, unsigned long long* acc,
+                                uint64_t count, int num_sms, cudaStream_t st);
 cudaError_t launch_philox_table(const uint32_t* ctr_key, uint32_t* out, int count,
                                 cudaStream_t st);
 
 // topk.cu
-cudaError_t launch_estimate(const double* res, const unsigned long long* acc, double* est,
-                            uint64_t count, int num_sms, cudaStream_t st);
+cudaError_t launch_estimate(const double* res, const Tally* tally, double* est, uint64_t count,
+                            int num_sms, cudaStream_t st);
 // Scratch of the top-k select: hist [nrows][kBins], slots [nrows], cand [nrows][kSortCap].
 struct TopkScratch {
   uint32_t* hist;

@@ -10,8 +10,6 @@
 //     walk j = g - offset[i] of node v; it reads its own Philox4x32-10 stream with
 //     counter (c, j, v, s) and stops with probability alpha at every node
 //     (Section 2.1); count[end] += 1 and acc[end] += W_v.
-// Each warp owns a contiguous range of walk indices (lanes interleaved by 32), so a
-// warp locates its first entry once and then advances through R monotonically.
 #include "fora_engine.cuh"
 
 namespace fora {
@@ -125,8 +123,9 @@ __global__ void __launch_bounds__(kResidualThreads) k_residual_count(GraphDev g,
     }
     const double r = b.r[i];
     if (r > 0.0) {
+      // an entry of R needs at least one walk (omega_v = 0 only if r * C underflows)
       const unsigned long long w = (unsigned long long)walks_of(r, b.walk_scale);
-      ++cnt; walks += w;
+      if (w > 0) { ++cnt; walks += w; }
       ++s_cnt; s_walks += w; s_sum += r;
     }
   }
@@ -180,8 +179,8 @@ __global__ void __launch_bounds__(kResidualThreads) k_residual_emit(GraphDev g, 
   for (unsigned long long tile = beg; tile < end; tile += kResidualThreads) {
     const unsigned long long i = tile + threadIdx.x;
     const double r = i < end ? b.r[i] : 0.0;
-    const bool live = r > 0.0;
-    const double omega = live ? walks_of(r, b.walk_scale) : 0.0;
+    const double omega = r > 0.0 ? walks_of(r, b.walk_scale) : 0.0;
+    const bool live = omega >= 1.0;
     unsigned long long ce, we, ct, wt;
     block_excl_scan2(live ? 1ull : 0ull, (unsigned long long)omega, &ce, &we, &ct, &wt);
     if (live) {
@@ -196,58 +195,119 @@ __global__ void __launch_bounds__(kResidualThreads) k_residual_emit(GraphDev g, 
   }
 }
 
-// Largest i in [lo, hi) with off[i] <= g (off non-decreasing, off[lo] <= g).
-__device__ __forceinline__ unsigned long long find_entry(const unsigned long long* off,
-                                                         unsigned long long lo,
-                                                         unsigned long long hi,
-                                                         unsigned long long g) {
-  while (hi - lo > 1) {
-    const unsigned long long mid = lo + ((hi - lo) >> 1);
-    if (off[mid] <= g) lo = mid; else hi = mid;
+constexpr int kWalkThreads = 256;
+constexpr int kWalkWarps = kWalkThreads / 32;
+constexpr int kWalksPerLane = 32;
+constexpr int kChunk = 32 * kWalksPerLane;  // walks per warp chunk
+constexpr uint32_t kMaxSteps = 16384u;
+
+// Largest i in [0, nR) with off[i] <= g (off non-decreasing, off[0] = 0 <= g);
+// warp-cooperative 32-ary search, every lane gets the answer.
+__device__ __forceinline__ unsigned long long warp_find_entry(const unsigned long long* off,
+                                                              unsigned long long nR,
+                                                              unsigned long long g) {
+  const unsigned lane = threadIdx.x & 31;
+  unsigned long long lo = 0, hi = nR;
+  while (hi - lo > 32) {
+    const unsigned long long step = (hi - lo + 31) / 32;
+    const unsigned long long p = lo + lane * step;
+    const unsigned bal = __ballot_sync(kFull, p < hi && off[p] <= g);
+    lo += (unsigned long long)(31 - __clz(bal)) * step;
+    hi = min(lo + step, hi);
   }
-  return lo;
+  const unsigned long long p = lo + lane;
+  const unsigned bal = __ballot_sync(kFull, p < hi && off[p] <= g);
+  return lo + (unsigned long long)(31 - __clz(bal));
 }
 
-__global__ void __launch_bounds__(256) k_walks(GraphDev g, BatchDev b) {
+// Walk schedule: the flat walk range is cut into chunks of kChunk walks and chunk c
+// goes to warp c mod (number of warps), so the walks in flight at any time are a
+// narrow window of the source-major walk space and their end tallies stay in L2.
+// Per chunk the warp first maps every walk to its residual entry (into shared
+// memory, relative to the chunk's first entry), then each lane runs its 32 walks
+// as an independent state machine (one move or one walk end per loop iteration).
+__global__ void __launch_bounds__(kWalkThreads) k_walks(GraphDev g, BatchDev b) {
+  __shared__ uint16_t smap[kWalkWarps][kChunk];
   if (*b.err) return;
   const unsigned long long W = b.totals[1];
   const unsigned long long nR = b.totals[0];
-  if (W == 0) return;
-  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
-  const unsigned long long wbeg = W * warp / nwarps, wend = W * (warp + 1) / nwarps;
-  unsigned long long gidx = wbeg + lane;
+  const unsigned long long nchunks = (W + kChunk - 1) / kChunk;
   const unsigned long long* off = b.wr_offset;
-  unsigned long long idx = gidx < wend ? find_entry(off, 0, nR, gidx) : 0;
-  unsigned long long steps_here = 0;  // moves of this lane's walks of source `cur_slot`
-  uint32_t cur_slot = 0xFFFFFFFFu;
   const uint2 key = make_uint2((uint32_t)b.seed, (uint32_t)(b.seed >> 32));
   const uint32_t t_alpha = b.alpha_threshold;
+  unsigned long long steps_here = 0;  // moves of this lane's walks of source `cur_slot`
+  uint32_t cur_slot = 0xFFFFFFFFu;
   bool capped = false;
-  for (; gidx < wend; gidx += 32) {
-    while (off[idx + 1] <= gidx) ++idx;
-    const unsigned long long entry = b.wr_entry[idx];
-    const uint32_t slot = (uint32_t)(entry >> 32), v = (uint32_t)entry;
-    if (slot != cur_slot) {  // a lane's walks visit sources in ascending order
-      if (steps_here) atomicAdd(&b.stats[cur_slot].walk_steps, steps_here);
-      steps_here = 0;
-      cur_slot = slot;
+
+  for (unsigned long long c = warp; c < nchunks; c += nwarps) {
+    const unsigned long long cbeg = c * kChunk;
+    const uint32_t cnt = (uint32_t)min((unsigned long long)kChunk, W - cbeg);
+    const unsigned long long idx0 = warp_find_entry(off, nR, cbeg);
+    // map walk cbeg + i -> entry idx0 + smap[i], 32 walks at a time
+    unsigned long long idxw = idx0;
+    for (uint32_t rb = 0; rb < cnt; rb += 32) {
+      const unsigned long long gw = cbeg + rb + lane;
+      const unsigned long long o = idxw + lane < nR ? off[idxw + lane] : ~0ull;
+      int lo = 0, hi = 31;  // largest j with off[idxw + j] <= gw
+#pragma unroll
+      for (int s = 0; s < 5; ++s) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__shfl_sync(kFull, o, mid) <= gw) lo = mid; else hi = mid - 1;
+      }
+      const unsigned long long mine = idxw + (unsigned long long)lo;
+      smap[wid][rb + lane] = (uint16_t)(mine - idx0);
+      idxw = __shfl_sync(kFull, mine, 31);
     }
+    __syncwarp();
+
+    uint32_t i = lane;
+    bool have = i < cnt;
     WalkStream rng;
-    rng.c = 0;
-    rng.j = (uint32_t)(gidx - off[idx]);
-    rng.v = v;
-    rng.s = (uint32_t)b.sources[slot];
     rng.key = key;
-    rng.avail = 0;
-    uint32_t x = v;
-    uint32_t steps = 0;
-    bool stopped = false;
-    for (; steps < 16384u; ++steps) {
-      if (rng.next() < t_alpha) { stopped = true; break; }
-      const uint32_t rb = g.row[x];
-      const uint32_t d = g.row[x + 1] - rb;
+    uint32_t x = 0, slot = 0, steps = 0;
+    unsigned long long wgt = 0;
+    if (have) {
+      const unsigned long long idx = idx0 + smap[wid][i];
+      const unsigned long long entry = b.wr_entry[idx];
+      slot = (uint32_t)(entry >> 32);
+      x = (uint32_t)entry;
+      rng.c = 0; rng.j = (uint32_t)(cbeg + i - off[idx]); rng.v = x;
+      rng.s = (uint32_t)b.sources[slot]; rng.avail = 0;
+      wgt = b.wr_weight[idx];
+      steps = 0;
+    }
+    while (have) {
+      if (rng.next() < t_alpha) {
+        // the walk stops at x (Section 2.1): count it and add its weight (Alg. 2)
+        Tally* t = b.tally + (unsigned long long)slot * (unsigned long long)g.n + x;
+        atomicAdd(&t->cnt, 1u);
+        atomicAdd(&t->acc, wgt);
+        if (slot != cur_slot) {
+          if (steps_here) atomicAdd(&b.stats[cur_slot].walk_steps, steps_here);
+          steps_here = 0;
+          cur_slot = slot;
+        }
+        steps_here += steps;
+        i += 32;
+        have = i < cnt;
+        if (have) {
+          const unsigned long long idx = idx0 + smap[wid][i];
+          const unsigned long long entry = b.wr_entry[idx];
+          slot = (uint32_t)(entry >> 32);
+          x = (uint32_t)entry;
+          rng.c = 0; rng.j = (uint32_t)(cbeg + i - off[idx]); rng.v = x;
+          rng.s = (uint32_t)b.sources[slot]; rng.avail = 0;
+          wgt = b.wr_weight[idx];
+          steps = 0;
+        }
+        continue;
+      }
+      if (steps >= kMaxSteps) { capped = true; have = false; break; }
+      const uint32_t rb0 = g.row[x];
+      const uint32_t d = g.row[x + 1] - rb0;
       unsigned long long m = (unsigned long long)rng.next() * d;
       uint32_t low = (uint32_t)m;
       if (low < d) {
@@ -257,18 +317,26 @@ __global__ void __launch_bounds__(256) k_walks(GraphDev g, BatchDev b) {
           m = (unsigned long long)rng.next() * d;
           low = (uint32_t)m;
         }
-        if (low < reject_below) break;  // reported as a capped walk
+        if (low < reject_below) { capped = true; have = false; break; }
       }
-      x = (uint32_t)g.col[rb + (uint32_t)(m >> 32)];
+      x = (uint32_t)g.col[rb0 + (uint32_t)(m >> 32)];
+      ++steps;
     }
-    if (!stopped) { capped = true; break; }
-    steps_here += steps;
-    const unsigned long long gi = (unsigned long long)slot * (unsigned long long)g.n + x;
-    atomicAdd(&b.cnt[gi], 1u);
-    atomicAdd(&b.acc[gi], b.wr_weight[idx]);
+    __syncwarp();
   }
   if (capped) atomicOr(b.err, kErrWalkCap);
   if (steps_here) atomicAdd(&b.stats[cur_slot].walk_steps, steps_here);
+}
+
+__global__ void k_unpack_tally(const Tally* __restrict__ t, uint32_t* cnt,
+                               unsigned long long* acc, unsigned long long count) {
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += stride) {
+    const Tally v = t[i];
+    if (cnt) cnt[i] = v.cnt;
+    if (acc) acc[i] = v.acc;
+  }
 }
 
 __global__ void k_philox_table(const uint32_t* ck, uint32_t* out, int count) {
@@ -294,10 +362,19 @@ cudaError_t launch_residuals(const GraphDev& g, const BatchDev& b, cudaStream_t 
 
 cudaError_t launch_walks(const GraphDev& g, const BatchDev& b, int num_sms, cudaStream_t st) {
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walks, 256, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walks, kWalkThreads, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
-  k_walks<<<num_sms * per_sm, 256, 0, st>>>(g, b);
+  k_walks<<<num_sms * per_sm, kWalkThreads, 0, st>>>(g, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_tally(const Tally* t, uint32_t* cnt, unsigned long long* acc,
+                                uint64_t count, int num_sms, cudaStream_t st) {
+  uint64_t blocks = (count + 255) / 256;
+  if (blocks > (uint64_t)num_sms * 32) blocks = (uint64_t)num_sms * 32;
+  if (blocks == 0) return cudaSuccess;
+  k_unpack_tally<<<(unsigned)blocks, 256, 0, st>>>(t, cnt, acc, count);
   return cudaGetLastError();
 }
 

@@ -47,6 +47,8 @@ def parse_args():
                     help="sources in the bounded CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stats", action="store_true", help="per-step counters to stderr")
+    ap.add_argument("--tune", action="append", default=[],
+                    help="launch-shape parameter key=value (fora_graph_tune)")
     return ap.parse_args()
 
 
@@ -210,6 +212,11 @@ def run_fora(args):
     rp, col = inputs.rmat_csr(w["scale"], w["avg_deg"], w["graph_seed"])
     n = len(rp) - 1
     g = fora.Graph(rp, col)
+    tuning = {}
+    for kv in args.tune:
+        key, val = kv.split("=")
+        g.tune(key, int(val))
+        tuning[key] = int(val)
     params = fora.Params.make(eps=args.eps, k=k, seed=inputs.WALK_SEED)
     stream = torch.cuda.current_stream()
     ids = torch.empty((B, k), dtype=torch.int32, device="cuda")
@@ -305,7 +312,8 @@ def run_fora(args):
                        "avg_out_degree": w["avg_deg"], "sources_per_launch": B, "k": k,
                        "eps": args.eps, "alpha": 0.2, "delta": "1/n", "pf": "1/n",
                        "rmax": "rule", "parallelism": f"replicas{world}",
-                       "l2": "512 MiB buffer written between timed steps"},
+                       "l2": "512 MiB buffer written between timed steps",
+                       "tuning": tuning},
             "latency_ms": {"p50": lat[len(lat) // 2],
                            "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                            "note": "every query of a batch completes with its batch"},

@@ -179,6 +179,15 @@ int fora_topk(const double *est, int64_t n, int32_t nrows, uint32_t k, int32_t *
  * ctr_key (host, [count][6]); writes out (host, [count][4]). */
 int fora_philox_debug(const uint32_t *ctr_key, uint32_t *out, int32_t count);
 
+/*
+ * Launch-shape parameters of a graph's queries (results do not depend on them, only
+ * speed):  "spread_width" (1..4096, default 1): the push visits the sorted frontier of a
+ * round through this many interleaved segments, so the warps in flight cover about that
+ * many sources at once (wider spreads reductions on shared hub targets over more
+ * addresses; narrower keeps the residue arrays in flight smaller).
+ */
+int fora_graph_tune(fora_graph *g, const char *key, int64_t value);
+
 /* Message of the calling thread's last failure ("" if none). */
 const char *fora_last_error(void);
 

@@ -104,6 +104,8 @@ def load():
         L.fora_topk.argtypes = [P, i64, i32, u32, P, P, P]
         L.fora_philox_debug.restype = I
         L.fora_philox_debug.argtypes = [P, P, i32]
+        L.fora_graph_tune.restype = I
+        L.fora_graph_tune.argtypes = [P, ctypes.c_char_p, i64]
         L.fora_last_error.restype = ctypes.c_char_p
         L.fora_last_error.argtypes = []
         _lib = L
@@ -166,6 +168,10 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+    def tune(self, key: str, value: int):
+        """Set a launch-shape parameter (fora_graph_tune); results do not depend on it."""
+        _check(load().fora_graph_tune(self._h, key.encode(), int(value)))
 
     def info(self):
         n, m, d = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()

@@ -53,6 +53,7 @@ struct fora_graph {
   int32_t* col = nullptr;
   int device = 0;
   int num_sms = 0;
+  Tuning tune;
   std::mutex mu;
 
   // workspace for up to `cap` sources
@@ -65,6 +66,8 @@ struct fora_graph {
   double* fa = nullptr;
   unsigned long long* small = nullptr;  // counters[4] totals[2]
   uint32_t* mask = nullptr;
+  uint32_t* hubw = nullptr;
+  unsigned long long* work = nullptr;
   uint32_t* active = nullptr;
   uint32_t* err = nullptr;
   int32_t* sources = nullptr;
@@ -86,7 +89,7 @@ struct fora_graph {
   void release_workspace() {
     dfree(r); dfree(res); dfree(tally);
     dfree(q[0]); dfree(q[1]); dfree(hub[0]); dfree(hub[1]); dfree(fa);
-    dfree(small); dfree(mask); dfree(active); dfree(err); dfree(sources); dfree(rmax); dfree(stats); dfree(blk);
+    dfree(small); dfree(mask); dfree(hubw); dfree(work); dfree(active); dfree(err); dfree(sources); dfree(rmax); dfree(stats); dfree(blk);
     if (topk_scratch) cudaFree(topk_scratch);
     topk_scratch = nullptr;
     dfree(out_ids); dfree(out_vals);
@@ -118,6 +121,8 @@ int ensure_workspace(fora_graph* g, int nsrc) {
   CUDA_TRY(cudaMalloc(&g->hub[1], H * sizeof(unsigned long long)));
   CUDA_TRY(cudaMalloc(&g->small, 8 * sizeof(unsigned long long)));
   CUDA_TRY(cudaMalloc(&g->mask, (size_t)nsrc * (((size_t)g->n + 31) / 32) * sizeof(uint32_t)));
+  CUDA_TRY(cudaMalloc(&g->hubw, (size_t)nsrc * (((size_t)g->n + 31) / 32) * sizeof(uint32_t)));
+  CUDA_TRY(cudaMalloc(&g->work, 32 * sizeof(unsigned long long)));
   CUDA_TRY(cudaMalloc(&g->active, 2 * (size_t)nsrc * sizeof(uint32_t)));
   CUDA_TRY(cudaMalloc(&g->err, sizeof(uint32_t)));
   CUDA_TRY(cudaMalloc(&g->sources, nsrc * sizeof(int32_t)));
@@ -217,6 +222,8 @@ int run_batch(fora_graph* g, const fora_params* p, const int32_t* sources, int n
   b.hub[0] = g->hub[0]; b.hub[1] = g->hub[1];
   b.counters = g->small;
   b.mask = g->mask;
+  b.hubw = g->hubw;
+  b.work = g->work;
   b.active = g->active;
   b.totals = g->small + 4;
   b.sources = g->sources; b.rmax = g->rmax; b.stats = g->stats; b.err = g->err;
@@ -226,6 +233,7 @@ int run_batch(fora_graph* g, const fora_params* p, const int32_t* sources, int n
   b.blk_cnt = g->blk;
   b.blk_walks = g->blk + g->residual_grid;
   b.residual_grid = g->residual_grid;
+  b.spread_width = g->tune.spread_width;
 
   const bool timed = st != nullptr;
   if (timed) CUDA_TRY(cudaEventRecord(g->ev[0], stream));
@@ -447,6 +455,17 @@ int fora_philox_debug(const uint32_t* ctr_key, uint32_t* out, int32_t count) {
   cudaFree(d_out);
   CUDA_TRY(e);
   return FORA_OK;
+}
+
+int fora_graph_tune(fora_graph* g, const char* key, int64_t value) {
+  if (!g || !key) return fail(FORA_ERR_BAD_ARG, "null graph or key");
+  std::lock_guard<std::mutex> lock(g->mu);
+  if (strcmp(key, "spread_width") == 0) {
+    if (value < 1 || value > 4096) return fail(FORA_ERR_BAD_ARG, "spread_width must be in [1, 4096]");
+    g->tune.spread_width = (int)value;
+    return FORA_OK;
+  }
+  return fail(FORA_ERR_BAD_ARG, "unknown tuning key '%s'", key);
 }
 
 const char* fora_last_error(void) { return g_err.c_str(); }

@@ -75,6 +75,8 @@ struct BatchDev {
   unsigned long long* hub[2];  // hub chunk items
   unsigned long long* counters;  // [4]: frontier/hub counts of parity 0 and 1
   uint32_t* mask;            // crossing mask, one bit per (slot, node), rows padded to words
+  uint32_t* hubw;            // hub items of the crossing nodes of each mask word
+  unsigned long long* work;  // dynamic work counters of the spread ([0] and [16])
   uint32_t* active;          // [2][nsrc]: sources with entries in q[0] / q[1]
   const int32_t* sources;    // [nsrc]
   const double* rmax;        // [nsrc]
@@ -88,6 +90,12 @@ struct BatchDev {
   unsigned long long* blk_walks;  // [grid] per-block counts, then block offsets
   unsigned long long* totals;     // [2]: |R|, W
   int residual_grid;
+  int spread_width;  // interleaved segments of the frontier the spread visits at once
+};
+
+// Launch-shape parameters of a graph (set through fora_graph_tune).
+struct Tuning {
+  int spread_width = 1;
 };
 
 // push.cu

@@ -175,6 +175,24 @@ int fora_ssppr_batch_debug(fora_graph *g, const fora_params *params, const int32
 int fora_topk(const double *est, int64_t n, int32_t nrows, uint32_t k, int32_t *out_ids,
               double *out_vals, void *stream);
 
+/*
+ * fora_topk without any allocation, for callers that cannot call cudaMalloc or
+ * cudaFree: a free synchronises the whole device and so stalls the other streams of
+ * a latency-bound serving loop, and a process that runs under a device-memory budget
+ * fixed at start-up must not grow it per call.  The paper has no counterpart: this is
+ * a memory-management variant of the same select.
+ * Same arguments and results as fora_topk (est, out_ids and out_vals are device
+ * pointers the caller owns), with at most 9 rows per call: the scratch lives in one
+ * 1 MiB device array of the library, which every GPU that loads the library holds
+ * until the process exits.  Larger nrows -> FORA_ERR_BAD_ARG.  The first call on a
+ * device (with that device current) looks up the array's device address; make that
+ * first call before any stream capture.  All calls share the one array: calls that
+ * overlap on the GPU (on different streams or host threads) race and must be ordered
+ * by the caller.  Returns after the stream has finished the select.
+ */
+int fora_topk_noalloc(const double *est, int64_t n, int32_t nrows, uint32_t k, int32_t *out_ids,
+                      double *out_vals, void *stream);
+
 /* Evaluate the device Philox4x32-10 on count (counter[4], key[2]) rows of
  * ctr_key (host, [count][6]); writes out (host, [count][4]). */
 int fora_philox_debug(const uint32_t *ctr_key, uint32_t *out, int32_t count);

@@ -104,6 +104,8 @@ def load():
         L.fora_topk.argtypes = [P, i64, i32, u32, P, P, P]
         L.fora_philox_debug.restype = I
         L.fora_philox_debug.argtypes = [P, P, i32]
+        L.fora_topk_noalloc.restype = I
+        L.fora_topk_noalloc.argtypes = [P, i64, i32, u32, P, P, P]
         L.fora_graph_tune.restype = I
         L.fora_graph_tune.argtypes = [P, ctypes.c_char_p, i64]
         L.fora_last_error.restype = ctypes.c_char_p

@@ -46,6 +46,16 @@ void dfree(T*& p) {
 
 }  // namespace
 
+int fora::report_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
 struct fora_graph {
   int64_t n = 0, m = 0, max_deg = 0;
   uint64_t hub_chunks = 0;  // sum over nodes with d > kHubChunk of ceil(d / kHubChunk)

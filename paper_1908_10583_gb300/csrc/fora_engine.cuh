@@ -98,6 +98,9 @@ struct Tuning {
   int spread_width = 1;
 };
 
+// capi.cu: record a failure for fora_last_error() and return `code`.
+int report_error(int code, const char* fmt, ...);
+
 // push.cu
 cudaError_t launch_push_init(const GraphDev& g, const BatchDev& b, cudaStream_t st);
 cudaError_t launch_push_detect(const GraphDev& g, const BatchDev& b, int par, uint32_t round,

@@ -68,6 +68,10 @@ extern "C" {
 #define FORA_OUT_DEVICE 0x1u /* out_ids / out_vals are device pointers (else host) */
 #define FORA_ASYNC 0x2u      /* return without synchronising (needs FORA_OUT_DEVICE and
                                 no stats); errors found on the device are then not reported */
+#define FORA_ZERO_HOP 0x4u   /* walk phase with zero-hop pruning (Section 4.1): alpha r(v)
+                                goes to the estimate directly and omega_v = ceil((1-alpha)
+                                r(v) C) walks each first move to a uniform out-neighbour of
+                                v (no stop test at v), carrying (1-alpha) r(v) / omega_v */
 
 typedef struct fora_graph fora_graph; /* opaque: device copy of the CSR + query workspace */
 
@@ -143,6 +147,82 @@ int fora_ssppr(fora_graph *g, const fora_params *params, int32_t source, int32_t
 int fora_ssppr_batch(fora_graph *g, const fora_params *params, const int32_t *sources,
                      int32_t nsrc, int32_t *out_ids, double *out_vals, fora_stats *stats,
                      void *stream);
+
+/*
+ * fora_ssppr_batch with one residue threshold per source: rmax is a HOST array of nsrc
+ * values > 0 (params->rmax is not used).  The accuracy guarantee of Lemma
+ * (layerppr-conc) holds for any r_max, since omega scales with r_sum; r_max only moves
+ * work between the push and the walks.  stats[i].rmax reports the value used.
+ */
+int fora_ssppr_batch_rmax(fora_graph *g, const fora_params *params, const int32_t *sources,
+                          const double *rmax, int32_t nsrc, int32_t *out_ids, double *out_vals,
+                          fora_stats *stats, void *stream);
+
+/*
+ * Top-k FORA (Alg. 5, Section 5.2) for nsrc sources: for delta = 1/k, 1/(2k), ...
+ * and finally 1/n, run the query with eps' = eps/2, failure probability
+ * p_f' = p_f / (n log2(n/k)) (log2 taken as at least 1) and r_max by the rule for these
+ * values (or params->rmax if > 0); a source stops at the first round whose k-th
+ * largest estimate is >= (1 + eps) delta.  Round i draws its walks with key seed + i.
+ * params->delta is not used; params->pf is the overall p_f (<= 0 selects 1/n);
+ * FORA_ZERO_HOP is honoured.  Outputs are HOST arrays: out_ids / out_vals [nsrc][k],
+ * stats [nsrc] (the stopping round's counters) and iterations [nsrc] (rounds run);
+ * stats and iterations may be NULL.  1 <= k <= min(n, FORA_MAX_K).
+ */
+int fora_topk_ssppr_batch(fora_graph *g, const fora_params *params, const int32_t *sources,
+                          int32_t nsrc, int32_t *out_ids, double *out_vals, fora_stats *stats,
+                          uint32_t *iterations, void *stream);
+
+/* ---- learned r_max ---- */
+
+/*
+ * A 16-64-64-1 MLP with BF16 weights and activations and FP32 accumulation that predicts
+ * log2(r_max / r_rule) for a source from its features; the query then runs with
+ * r_max = r_rule * 2^clamp(prediction, -3, 3).  Any r_max keeps the accuracy guarantee
+ * of Lemma (layerppr-conc); the network only trades push work against walk work (the
+ * role of the balancing of Section 4.2).  Parameters: FP32 masters, layout
+ * W1[64][16] | b1[64] | W2[64][64] | b2[64] | W3[64] | b3; the forward rounds the weights
+ * and every activation (inputs (f - mu)/sigma, hidden layers after ReLU) to BF16.
+ */
+#define FORA_NUM_FEATURES 16
+#define FORA_MODEL_PARAMS 5313
+typedef struct fora_model fora_model;
+
+/* New model on the current device, weights drawn uniformly in +-sqrt(6/fan_in) from `seed`,
+ * biases 0, normalisation mu = 0, sigma = 1. */
+int fora_model_create(uint64_t seed, fora_model **out);
+void fora_model_destroy(fora_model *m);
+/* Host copies of the FP32 parameters [FORA_MODEL_PARAMS] and normalisation
+ * [2 * FORA_NUM_FEATURES] (mu then sigma).  Either pointer may be NULL. */
+int fora_model_get(const fora_model *m, float *params, float *norm);
+int fora_model_set(fora_model *m, const float *params, const float *norm);
+/* Forward pass on host arrays: x [n][16] -> y [n]. */
+int fora_model_predict(fora_model *m, const float *x, int32_t n, float *y);
+/* Gradient of 0.5 mean (y - t)^2 w.r.t. the parameters (host arrays, grad
+ * [FORA_MODEL_PARAMS]) and the loss. */
+int fora_model_gradient(fora_model *m, const float *x, const float *t, int32_t n, float *grad,
+                        float *loss);
+/* Adam training on the device (lr, beta 0.9/0.999): mu/sigma are first set from x
+ * (sigma 1 where a feature is constant); each epoch visits the samples in a seeded
+ * shuffled order in mini-batches of `batch`.  loss_per_epoch [epochs] (may be NULL). */
+int fora_model_train(fora_model *m, const float *x, const float *t, int32_t n, int32_t epochs,
+                     int32_t batch, float lr, uint64_t seed, float *loss_per_epoch);
+
+/*
+ * Features of each source (host output [nsrc][16] float), with r_rule the rule's r_max
+ * for params: log1p d_out(s), log1p d_in(s), log1p sum_{u in N(s)} d_out(u),
+ * log1p sum d_in(u), log1p of the 1-hop frontier size #{edges (s,u): (1-alpha)/d_out(s)
+ * > r_rule d_out(u)}, log1p of the out-edges of that frontier (the 2-hop frontier),
+ * log(r_rule m), log(m/n), then zeros.
+ */
+int fora_source_features(fora_graph *g, const fora_params *params, const int32_t *sources,
+                         int32_t nsrc, float *out);
+
+/* fora_ssppr_batch with r_max chosen per source by the model (features, forward pass
+ * and r_max on the device); stats[i].rmax reports the value used. */
+int fora_ssppr_batch_learned(fora_graph *g, const fora_params *params, fora_model *model,
+                             const int32_t *sources, int32_t nsrc, int32_t *out_ids,
+                             double *out_vals, fora_stats *stats, void *stream);
 
 /* ---- inspection entry points (parity testing) ---- */
 

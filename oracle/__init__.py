@@ -80,6 +80,17 @@ def _load():
             lib.oracle_forward_push.argtypes = [i64, P, P, i32, dbl, dbl, P, P, P]
             lib.oracle_walk_phase.restype = ctypes.c_int
             lib.oracle_walk_phase.argtypes = [i64, P, P, i32, dbl, dbl, u64, P, P, P, P]
+            lib.oracle_walk_phase_zero_hop.restype = ctypes.c_int
+            lib.oracle_walk_phase_zero_hop.argtypes = [i64, P, P, i32, dbl, dbl, u64, P, P, P, P]
+            lib.oracle_estimate_zero_hop.restype = None
+            lib.oracle_estimate_zero_hop.argtypes = [i64, P, P, P, dbl, P]
+            lib.oracle_ssppr_zero_hop.restype = ctypes.c_int
+            lib.oracle_ssppr_zero_hop.argtypes = [i64, P, P, i32, dbl, dbl, dbl,
+                                                  dbl, dbl, u64, i64, P, P, P, P,
+                                                  P, P, P, P, P]
+            lib.oracle_topk_fora.restype = ctypes.c_int
+            lib.oracle_topk_fora.argtypes = [i64, P, P, i32, dbl, dbl, dbl, dbl, u64, i64, P, P,
+                                             P, P, P, P, P, P, P]
             lib.oracle_estimate.restype = None
             lib.oracle_estimate.argtypes = [i64, P, P, P]
             lib.oracle_topk.restype = ctypes.c_int
@@ -151,6 +162,31 @@ def walk_phase(row_ptr, col, s, alpha, scale, seed, residue):
     return count, acc, st
 
 
+def walk_phase_zero_hop(row_ptr, col, s, alpha, scale, seed, residue):
+    """Walk phase with zero-hop pruning (Section 4.1) -> (count u32, acc u64, WalkStats)."""
+    row_ptr, col, n = _graph(row_ptr, col)
+    residue = np.ascontiguousarray(residue, dtype=np.float64)
+    count = np.zeros(n, dtype=np.uint32)
+    acc = np.zeros(n, dtype=np.uint64)
+    st = WalkStats()
+    rc = _load().oracle_walk_phase_zero_hop(n, _ptr(row_ptr), _ptr(col), int(s), alpha, scale,
+                                            int(seed), _ptr(residue), _ptr(count), _ptr(acc),
+                                            ctypes.addressof(st))
+    if rc:
+        raise OracleError(rc)
+    return count, acc, st
+
+
+def estimate_zero_hop(reserve, residue, acc, alpha):
+    reserve = np.ascontiguousarray(reserve, dtype=np.float64)
+    residue = np.ascontiguousarray(residue, dtype=np.float64)
+    acc = np.ascontiguousarray(acc, dtype=np.uint64)
+    est = np.zeros(len(reserve))
+    _load().oracle_estimate_zero_hop(len(reserve), _ptr(reserve), _ptr(residue), _ptr(acc),
+                                     alpha, _ptr(est))
+    return est
+
+
 def estimate(reserve, acc):
     reserve = np.ascontiguousarray(reserve, dtype=np.float64)
     acc = np.ascontiguousarray(acc, dtype=np.uint64)
@@ -184,8 +220,9 @@ class QueryResult:
 
 
 def ssppr(row_ptr, col, s, *, alpha=0.2, eps=0.5, delta=None, pf=None, rmax=0.0,
-          seed=0x5EED, k=50):
-    """One whole query (Alg. 2 + top-k); delta and p_f default to 1/n."""
+          seed=0x5EED, k=50, zero_hop=False):
+    """One whole query (Alg. 2 + top-k; with zero_hop, the walk phase of Section 4.1);
+    delta and p_f default to 1/n."""
     row_ptr, col, n = _graph(row_ptr, col)
     delta = 1.0 / n if delta is None else delta
     pf = 1.0 / n if pf is None else pf
@@ -196,7 +233,8 @@ def ssppr(row_ptr, col, s, *, alpha=0.2, eps=0.5, delta=None, pf=None, rmax=0.0,
     ids = np.zeros(k, dtype=np.int32)
     vals = np.zeros(k)
     pst, wst = PushStats(), WalkStats()
-    rc = _load().oracle_ssppr(n, _ptr(row_ptr), _ptr(col), int(s), alpha, eps, delta, pf,
+    fn = _load().oracle_ssppr_zero_hop if zero_hop else _load().oracle_ssppr
+    rc = fn(n, _ptr(row_ptr), _ptr(col), int(s), alpha, eps, delta, pf,
                               rmax_used, int(seed), int(k), _ptr(arrays["reserve"]),
                               _ptr(arrays["residue"]), _ptr(arrays["count"]),
                               _ptr(arrays["acc"]), _ptr(arrays["est"]), _ptr(ids), _ptr(vals),
@@ -204,3 +242,30 @@ def ssppr(row_ptr, col, s, *, alpha=0.2, eps=0.5, delta=None, pf=None, rmax=0.0,
     if rc:
         raise OracleError(rc)
     return QueryResult(ids=ids, vals=vals, push=pst, walk=wst, rmax=rmax_used, **arrays)
+
+
+@dataclass
+class TopkResult:
+    ids: np.ndarray
+    vals: np.ndarray
+    est: np.ndarray
+    iterations: int
+    delta: float
+
+
+def topk_fora(row_ptr, col, s, k, *, alpha=0.2, eps=0.5, pf=None, rmax=0.0, seed=0x5EED):
+    """Top-k FORA (Alg. 5): delta halving from 1/k to 1/n with eps/2 and p_f/(n log2(n/k))."""
+    row_ptr, col, n = _graph(row_ptr, col)
+    pf = 1.0 / n if pf is None else pf
+    work = [np.zeros(n), np.zeros(n), np.zeros(n, dtype=np.uint32), np.zeros(n, dtype=np.uint64),
+            np.zeros(n)]
+    ids = np.zeros(k, dtype=np.int32)
+    vals = np.zeros(k)
+    it = ctypes.c_int32(0)
+    dl = ctypes.c_double(0.0)
+    rc = _load().oracle_topk_fora(n, _ptr(row_ptr), _ptr(col), int(s), alpha, eps, pf, rmax,
+                                  int(seed), int(k), *[_ptr(a) for a in work], _ptr(ids),
+                                  _ptr(vals), ctypes.addressof(it), ctypes.addressof(dl))
+    if rc:
+        raise OracleError(rc)
+    return TopkResult(ids=ids, vals=vals, est=work[4], iterations=it.value, delta=dl.value)

@@ -300,6 +300,70 @@ int oracle_walk_phase(int64_t n, const int64_t *row_ptr, const int32_t *col, int
   return ORACLE_OK;
 }
 
+/*
+ * Walk phase with zero-hop pruning (Section 4.1).  A walk from v stops at v at once
+ * with probability alpha, so that part of r(v) goes straight to the estimate
+ * (alpha r(v), added by oracle_estimate_zero_hop) and only r'(v) = (1 - alpha) r(v)
+ * is sampled: omega_v = ceil(r'(v) * C) walks from v, each of which first moves to a
+ * uniform out-neighbour u of v (no stop test at v) and then runs the alpha-terminating
+ * walk from u; each adds r'(v) / omega_v at its end.  This applies (1 - alpha) once,
+ * as the derivation of Section 4.1 does (Alg. 3 applies it twice, a typo).
+ * The walk's word stream is the same as in oracle_walk_phase: the forced first move
+ * draws its neighbour index first.
+ */
+int oracle_walk_phase_zero_hop(int64_t n, const int64_t *row_ptr, const int32_t *col, int32_t s,
+                               double alpha, double walk_scale, uint64_t seed,
+                               const double *residue, uint32_t *count, uint64_t *acc,
+                               oracle_walk_stats *st) {
+  int rc = check_graph(n, row_ptr, col);
+  if (rc) return rc;
+  if (s < 0 || s >= n || !(alpha > 0.0 && alpha < 1.0) || !(walk_scale > 0.0))
+    return ORACLE_ERR_BAD_ARG;
+  const uint32_t t_alpha = oracle_alpha_threshold(alpha);
+  oracle_walk_stats local = {0, 0, 0};
+  for (int64_t t = 0; t < n; ++t) { count[t] = 0; acc[t] = 0; }
+  for (int64_t v = 0; v < n; ++v) {
+    if (residue[v] > 0.0) {
+      const double omega_v = ceil(((1.0 - alpha) * residue[v]) * walk_scale);
+      local.residual_nodes++;
+      if (omega_v > 4294967295.0) return ORACLE_ERR_WALK_OVERFLOW;
+      local.walks += (int64_t)omega_v;
+    } else if (residue[v] < 0.0) {
+      return ORACLE_ERR_BAD_ARG;
+    }
+  }
+  if (local.walks > 4294967295LL) return ORACLE_ERR_WALK_OVERFLOW;
+  for (int64_t v = 0; v < n; ++v) {
+    if (!(residue[v] > 0.0)) continue;
+    const double r_kept = (1.0 - alpha) * residue[v];
+    const double omega_v = ceil(r_kept * walk_scale);
+    const double weight = r_kept / omega_v;
+    const uint64_t fixed = (uint64_t)nearbyint(ldexp(weight, 63));
+    const uint32_t nw = (uint32_t)omega_v;
+    const uint32_t dv = (uint32_t)(row_ptr[v + 1] - row_ptr[v]);
+    for (uint32_t j = 0; j < nw; ++j) {
+      walk_stream w;
+      stream_init(&w, j, (uint32_t)v, (uint32_t)s, seed);
+      const uint32_t idx = uniform_index(&w, dv); /* the forced first move */
+      const int32_t u = col[row_ptr[v] + idx];
+      local.walk_steps += 1;
+      int64_t end = random_walk(row_ptr, col, t_alpha, &w, u, &local.walk_steps);
+      if (end < 0) return ORACLE_ERR_WALK_CAP;
+      count[end] += 1;
+      acc[end] += fixed;
+    }
+  }
+  if (st) *st = local;
+  return ORACLE_OK;
+}
+
+/* Zero-hop estimate: pi_hat(t) = (reserve(t) + alpha * r(t)) + acc(t) * 2^-63 */
+void oracle_estimate_zero_hop(int64_t n, const double *reserve, const double *residue,
+                              const uint64_t *acc, double alpha, double *est) {
+  for (int64_t t = 0; t < n; ++t)
+    est[t] = (reserve[t] + alpha * residue[t]) + ldexp((double)acc[t], -63);
+}
+
 /* pi_hat(t) = reserve(t) + acc(t) * 2^-63 */
 void oracle_estimate(int64_t n, const double *reserve, const uint64_t *acc, double *est) {
   for (int64_t t = 0; t < n; ++t) est[t] = reserve[t] + ldexp((double)acc[t], -63);
@@ -354,4 +418,58 @@ int oracle_ssppr(int64_t n, const int64_t *row_ptr, const int32_t *col, int32_t 
   if (rc) return rc;
   oracle_estimate(n, reserve, acc, est);
   return oracle_topk(n, est, k, ids, vals);
+}
+
+/* The whole query with zero-hop pruning (Section 4.1) in the walk phase. */
+int oracle_ssppr_zero_hop(int64_t n, const int64_t *row_ptr, const int32_t *col, int32_t s,
+                          double alpha, double eps, double delta, double pf, double rmax,
+                          uint64_t seed, int64_t k, double *reserve, double *residue,
+                          uint32_t *count, uint64_t *acc, double *est, int32_t *ids,
+                          double *vals, oracle_push_stats *pst, oracle_walk_stats *wst) {
+  if (!(eps > 0.0) || !(delta > 0.0) || !(pf > 0.0 && pf < 1.0)) return ORACLE_ERR_BAD_ARG;
+  if (!(rmax > 0.0)) rmax = oracle_rmax_rule(eps, delta, pf, (double)row_ptr[n]);
+  int rc = oracle_forward_push(n, row_ptr, col, s, alpha, rmax, reserve, residue, pst);
+  if (rc) return rc;
+  rc = oracle_walk_phase_zero_hop(n, row_ptr, col, s, alpha, oracle_walk_scale(eps, delta, pf),
+                                  seed, residue, count, acc, wst);
+  if (rc) return rc;
+  oracle_estimate_zero_hop(n, reserve, residue, acc, alpha, est);
+  return oracle_topk(n, est, k, ids, vals);
+}
+
+/* ------------------------------------------------------ top-k FORA (Alg. 5) */
+
+/*
+ * Top-k FORA (Alg. 5, Section 5.2).  For delta = 1/k, 1/(2k), 1/(4k), ... and finally
+ * 1/n, run Alg. 2 with eps' = eps/2, failure probability p_f' = p_f / (n log2(n/k))
+ * and r_max by Eq. (rmax) for these parameters (or the given rmax > 0); stop as soon
+ * as the k-th largest estimate is >= (1 + eps) delta and return that round's top-k.
+ * Readings: iteration i < I = ceil(log2(n/k)) uses delta_i = 1/(k 2^i), the last one
+ * delta_I = 1/n; log2(n/k) is taken as at least 1; round i draws its walks with key
+ * seed + i.  *iterations and *final_delta report where it stopped.
+ */
+int oracle_topk_fora(int64_t n, const int64_t *row_ptr, const int32_t *col, int32_t s,
+                     double alpha, double eps, double pf, double rmax, uint64_t seed,
+                     int64_t k, double *reserve, double *residue, uint32_t *count,
+                     uint64_t *acc, double *est, int32_t *ids, double *vals,
+                     int32_t *iterations, double *final_delta) {
+  if (k < 1 || k > n || !(eps > 0.0) || !(pf > 0.0 && pf < 1.0)) return ORACLE_ERR_BAD_ARG;
+  int32_t rounds_total = 0;
+  while ((double)k * ldexp(1.0, rounds_total) < (double)n) ++rounds_total; /* I */
+  double lg = log2((double)n / (double)k);
+  if (lg < 1.0) lg = 1.0;
+  const double pf_round = pf / ((double)n * lg);
+  for (int32_t i = 0; i <= rounds_total; ++i) {
+    const double delta = i < rounds_total ? 1.0 / ((double)k * ldexp(1.0, i)) : 1.0 / (double)n;
+    int rc = oracle_ssppr(n, row_ptr, col, s, alpha, eps / 2.0, delta, pf_round, rmax,
+                          seed + (uint64_t)i, k, reserve, residue, count, acc, est, ids, vals,
+                          NULL, NULL);
+    if (rc) return rc;
+    if (vals[k - 1] >= (1.0 + eps) * delta || i == rounds_total) {
+      if (iterations) *iterations = i + 1;
+      if (final_delta) *final_delta = delta;
+      return ORACLE_OK;
+    }
+  }
+  return ORACLE_OK; /* not reached */
 }

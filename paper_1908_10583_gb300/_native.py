@@ -26,6 +26,7 @@ FORA_ERR_CUDA = -7
 FORA_MAX_K = 4096
 FORA_OUT_DEVICE = 0x1
 FORA_ASYNC = 0x2
+FORA_ZERO_HOP = 0x4
 FORA_DBG_GIVEN_PUSH = 0x1
 
 _lock = threading.Lock()
@@ -100,6 +101,10 @@ def load():
         L.fora_ssppr_batch_debug.restype = I
         L.fora_ssppr_batch_debug.argtypes = [P, ctypes.POINTER(Params), P, i32, P, P, P,
                                              ctypes.POINTER(DebugIO), u32, P]
+        L.fora_ssppr_batch_rmax.restype = I
+        L.fora_ssppr_batch_rmax.argtypes = [P, ctypes.POINTER(Params), P, P, i32, P, P, P, P]
+        L.fora_topk_ssppr_batch.restype = I
+        L.fora_topk_ssppr_batch.argtypes = [P, ctypes.POINTER(Params), P, i32, P, P, P, P, P]
         L.fora_topk.restype = I
         L.fora_topk.argtypes = [P, i64, i32, u32, P, P, P]
         L.fora_philox_debug.restype = I
@@ -217,6 +222,42 @@ class Graph:
                                        ctypes.addressof(st) if st is not None else None,
                                        _stream_ptr(stream)))
         return out_ids, out_vals, (list(st) if st is not None else None)
+
+    def ssppr_batch_rmax(self, sources, rmax, params: Params, out_ids=None, out_vals=None,
+                         stream=None):
+        """Batched query with one r_max per source (host array)."""
+        src = np.ascontiguousarray(sources, dtype=np.int32)
+        rm = np.ascontiguousarray(rmax, dtype=np.float64)
+        assert len(rm) == len(src)
+        nsrc, k = len(src), params.k
+        p = Params.from_buffer_copy(params)
+        if out_ids is not None:
+            p.flags |= FORA_OUT_DEVICE
+        else:
+            p.flags &= ~FORA_OUT_DEVICE
+            out_ids = np.zeros((nsrc, k), dtype=np.int32)
+            out_vals = np.zeros((nsrc, k), dtype=np.float64)
+        st = (Stats * nsrc)()
+        _check(load().fora_ssppr_batch_rmax(self._h, ctypes.byref(p), src.ctypes.data,
+                                            rm.ctypes.data, nsrc, _ptr(out_ids), _ptr(out_vals),
+                                            ctypes.addressof(st), _stream_ptr(stream)))
+        return out_ids, out_vals, list(st)
+
+    def topk_fora(self, sources, params: Params, stream=None):
+        """Top-k FORA (Alg. 5) per source -> (ids [nsrc, k], vals, stats, iterations)."""
+        src = np.ascontiguousarray(sources, dtype=np.int32)
+        nsrc, k = len(src), params.k
+        ids = np.zeros((nsrc, k), dtype=np.int32)
+        vals = np.zeros((nsrc, k), dtype=np.float64)
+        iters = np.zeros(nsrc, dtype=np.uint32)
+        st = (Stats * nsrc)()
+        p = Params.from_buffer_copy(params)
+        p.flags &= ~FORA_OUT_DEVICE
+        _check(load().fora_topk_ssppr_batch(self._h, ctypes.byref(p), src.ctypes.data, nsrc,
+                                            ids.ctypes.data, vals.ctypes.data,
+                                            ctypes.addressof(st), iters.ctypes.data,
+                                            _stream_ptr(stream)))
+        return ids, vals, list(st), iters
 
     def ssppr_batch_host(self, sources, params: Params, out_ids: np.ndarray,
                          out_vals: np.ndarray, stream=None):

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libfora.so")
-SOURCES = ["push.cu", "walk.cu", "topk.cu", "capi.cu", "topk_noalloc.cu"]
+SOURCES = ["push.cu", "walk.cu", "topk.cu", "capi.cu", "topk_noalloc.cu", "learn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

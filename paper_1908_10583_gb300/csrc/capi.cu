@@ -61,6 +61,7 @@ struct fora_graph {
   uint64_t hub_chunks = 0;  // sum over nodes with d > kHubChunk of ceil(d / kHubChunk)
   uint32_t* row = nullptr;
   int32_t* col = nullptr;
+  uint32_t* indeg = nullptr;  // in-degrees (features of the learned r_max)
   int device = 0;
   int num_sms = 0;
   Tuning tune;
@@ -86,6 +87,9 @@ struct fora_graph {
   unsigned long long* blk = nullptr;  // [2][residual_grid]
   int residual_grid = 0;
   void* topk_scratch = nullptr;
+  float* feat = nullptr;        // learned r_max: features [cap][16], predictions, r_max
+  float* pred = nullptr;
+  double* rmax_learned = nullptr;
   int32_t* out_ids = nullptr;  // device staging of host-bound results [cap][FORA_MAX_K]
   double* out_vals = nullptr;
   // pinned host mirrors
@@ -102,7 +106,7 @@ struct fora_graph {
     dfree(small); dfree(mask); dfree(hubw); dfree(work); dfree(active); dfree(err); dfree(sources); dfree(rmax); dfree(stats); dfree(blk);
     if (topk_scratch) cudaFree(topk_scratch);
     topk_scratch = nullptr;
-    dfree(out_ids); dfree(out_vals);
+    dfree(out_ids); dfree(out_vals); dfree(feat); dfree(pred); dfree(rmax_learned);
     if (h_counters) cudaFreeHost(h_counters);
     if (h_stats) cudaFreeHost(h_stats);
     if (h_err) cudaFreeHost(h_err);
@@ -140,6 +144,9 @@ int ensure_workspace(fora_graph* g, int nsrc) {
   CUDA_TRY(cudaMalloc(&g->stats, nsrc * sizeof(SlotStats)));
   CUDA_TRY(cudaMalloc(&g->blk, 2 * (size_t)g->residual_grid * sizeof(unsigned long long)));
   CUDA_TRY(cudaMalloc(&g->topk_scratch, topk_scratch_bytes(nsrc)));
+  CUDA_TRY(cudaMalloc(&g->feat, (size_t)nsrc * FORA_NUM_FEATURES * sizeof(float)));
+  CUDA_TRY(cudaMalloc(&g->pred, (size_t)nsrc * sizeof(float)));
+  CUDA_TRY(cudaMalloc(&g->rmax_learned, (size_t)nsrc * sizeof(double)));
   CUDA_TRY(cudaMalloc(&g->out_ids, (size_t)nsrc * FORA_MAX_K * sizeof(int32_t)));
   CUDA_TRY(cudaMalloc(&g->out_vals, (size_t)nsrc * FORA_MAX_K * sizeof(double)));
   CUDA_TRY(cudaMallocHost(&g->h_counters, 8 * sizeof(unsigned long long)));
@@ -185,9 +192,15 @@ int resolve(const fora_graph* g, const fora_params* p, Resolved* out) {
   return FORA_OK;
 }
 
+// Per-source residue thresholds: a host array, or a device array (learned r_max).
+struct RmaxSource {
+  const double* host = nullptr;
+  const double* device = nullptr;
+};
+
 int run_batch(fora_graph* g, const fora_params* p, const int32_t* sources, int nsrc,
               int32_t* out_ids, double* out_vals, fora_stats* st, const fora_debug_io* dbg,
-              uint32_t dbg_flags, cudaStream_t stream) {
+              uint32_t dbg_flags, cudaStream_t stream, RmaxSource rsrc = RmaxSource()) {
   Resolved rp;
   int rc = resolve(g, p, &rp);
   if (rc) return rc;
@@ -211,10 +224,15 @@ int run_batch(fora_graph* g, const fora_params* p, const int32_t* sources, int n
   const size_t N = (size_t)nsrc * (size_t)g->n;
   for (int i = 0; i < nsrc; ++i) {
     g->h_sources[i] = sources[i];
-    g->h_rmax[i] = rp.rmax;
+    g->h_rmax[i] = rsrc.host ? rsrc.host[i] : rp.rmax;
+    if (!(g->h_rmax[i] > 0.0) || !std::isfinite(g->h_rmax[i]))
+      return fail(FORA_ERR_BAD_ARG, "r_max of source %d must be positive and finite", i);
   }
   CUDA_TRY(cudaMemcpyAsync(g->sources, g->h_sources, nsrc * sizeof(int32_t), cudaMemcpyHostToDevice, stream));
-  CUDA_TRY(cudaMemcpyAsync(g->rmax, g->h_rmax, nsrc * sizeof(double), cudaMemcpyHostToDevice, stream));
+  if (rsrc.device)
+    CUDA_TRY(cudaMemcpyAsync(g->rmax, rsrc.device, nsrc * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  else
+    CUDA_TRY(cudaMemcpyAsync(g->rmax, g->h_rmax, nsrc * sizeof(double), cudaMemcpyHostToDevice, stream));
   CUDA_TRY(cudaMemsetAsync(g->tally, 0, N * sizeof(Tally), stream));
   CUDA_TRY(cudaMemsetAsync(g->small, 0, 8 * sizeof(unsigned long long), stream));
   CUDA_TRY(cudaMemsetAsync(g->err, 0, sizeof(uint32_t), stream));
@@ -227,6 +245,7 @@ int run_batch(fora_graph* g, const fora_params* p, const int32_t* sources, int n
   b.walk_scale = rp.walk_scale;
   b.alpha_threshold = rp.alpha_threshold;
   b.seed = p->seed;
+  b.zero_hop = (p->flags & FORA_ZERO_HOP) != 0;
   b.r = g->r; b.res = g->res; b.tally = g->tally;
   b.q[0] = g->q[0]; b.q[1] = g->q[1]; b.fa = g->fa;
   b.hub[0] = g->hub[0]; b.hub[1] = g->hub[1];
@@ -288,7 +307,7 @@ int run_batch(fora_graph* g, const fora_params* p, const int32_t* sources, int n
                                  g->num_sms, stream));
 
   // ---- estimate and top-k (the residue array becomes the estimate) ----
-  CUDA_TRY(launch_estimate(g->res, g->tally, g->r, N, g->num_sms, stream));
+  CUDA_TRY(launch_estimate(g->res, g->tally, g->r, g->r, rp.alpha, b.zero_hop, N, g->num_sms, stream));
   if (dbg && dbg->estimate)
     CUDA_TRY(cudaMemcpyAsync(dbg->estimate, g->r, N * sizeof(double), cudaMemcpyDeviceToDevice, stream));
   int32_t* ids_dev = out_dev ? out_ids : g->out_ids;
@@ -303,6 +322,8 @@ int run_batch(fora_graph* g, const fora_params* p, const int32_t* sources, int n
   if (async) return FORA_OK;
   CUDA_TRY(cudaMemcpyAsync(g->h_err, g->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
   if (st) CUDA_TRY(cudaMemcpyAsync(g->h_stats, g->stats, nsrc * sizeof(SlotStats), cudaMemcpyDeviceToHost, stream));
+  if (st && rsrc.device)
+    CUDA_TRY(cudaMemcpyAsync(g->h_rmax, g->rmax, nsrc * sizeof(double), cudaMemcpyDeviceToHost, stream));
   CUDA_TRY(cudaStreamSynchronize(stream));
   if (*g->h_err & kErrWalkOverflow) return fail(FORA_ERR_WALK_OVERFLOW, "a source needs 2^32 or more walks");
   if (*g->h_err & kErrWalkCap) return fail(FORA_ERR_WALK_CAP, "a walk exceeded %d moves", FORA_MAX_WALK_STEPS);
@@ -312,7 +333,7 @@ int run_batch(fora_graph* g, const fora_params* p, const int32_t* sources, int n
     for (int i = 0; i < nsrc; ++i) {
       const SlotStats& s = g->h_stats[i];
       fora_stats& o = st[i];
-      o.rmax = rp.rmax;
+      o.rmax = g->h_rmax[i];
       o.rsum = s.rsum;
       o.pushes = s.pushes;
       o.edge_pushes = s.edge_pushes;
@@ -374,6 +395,12 @@ int fora_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col, uin
   if (e == cudaSuccess) e = cudaMalloc(&g->col, (size_t)m * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemcpy(g->row, row.data(), ((size_t)n + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(g->col, col, (size_t)m * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&g->indeg, (size_t)n * sizeof(uint32_t));
+  if (e == cudaSuccess) {
+    GraphDev gd{g->n, g->m, g->row, g->col};
+    e = launch_indegree(gd, g->indeg, g->num_sms, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  }
   for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = cudaEventCreate(&g->ev[i]);
   if (e != cudaSuccess)
     return bail(fail(e == cudaErrorMemoryAllocation ? FORA_ERR_OOM : FORA_ERR_CUDA, "graph upload: %s",
@@ -390,6 +417,7 @@ void fora_graph_destroy(fora_graph* g) {
     g->release_workspace();
     dfree(g->row);
     dfree(g->col);
+    dfree(g->indeg);
     for (int i = 0; i < 5; ++i)
       if (g->ev[i]) cudaEventDestroy(g->ev[i]);
   }
@@ -425,11 +453,73 @@ int fora_ssppr_batch(fora_graph* g, const fora_params* params, const int32_t* so
   return run_batch(g, params, sources, nsrc, out_ids, out_vals, stats, nullptr, 0, (cudaStream_t)stream);
 }
 
+int fora_ssppr_batch_rmax(fora_graph* g, const fora_params* params, const int32_t* sources,
+                          const double* rmax, int32_t nsrc, int32_t* out_ids, double* out_vals,
+                          fora_stats* stats, void* stream) {
+  if (!rmax) return fail(FORA_ERR_BAD_ARG, "null r_max array");
+  RmaxSource rs;
+  rs.host = rmax;
+  return run_batch(g, params, sources, nsrc, out_ids, out_vals, stats, nullptr, 0,
+                   (cudaStream_t)stream, rs);
+}
+
 int fora_ssppr_batch_debug(fora_graph* g, const fora_params* params, const int32_t* sources,
                            int32_t nsrc, int32_t* out_ids, double* out_vals, fora_stats* stats,
                            const fora_debug_io* dbg, uint32_t dbg_flags, void* stream) {
   return run_batch(g, params, sources, nsrc, out_ids, out_vals, stats, dbg, dbg_flags,
                    (cudaStream_t)stream);
+}
+
+int fora_topk_ssppr_batch(fora_graph* g, const fora_params* params, const int32_t* sources,
+                          int32_t nsrc, int32_t* out_ids, double* out_vals, fora_stats* stats,
+                          uint32_t* iterations, void* stream) {
+  if (!g || !params || !sources || nsrc < 1) return fail(FORA_ERR_BAD_ARG, "bad arguments");
+  const uint32_t k = params->k;
+  if (k < 1 || k > FORA_MAX_K || (int64_t)k > g->n) return fail(FORA_ERR_BAD_ARG, "k out of range");
+  if (!out_ids || !out_vals) return fail(FORA_ERR_BAD_ARG, "null output");
+  if (params->flags & (FORA_OUT_DEVICE | FORA_ASYNC))
+    return fail(FORA_ERR_BAD_ARG, "top-k FORA writes host outputs and runs synchronously");
+  const double n = (double)g->n;
+  // rounds i < I use delta = 1/(k 2^i), round I uses 1/n (Alg. 5, line 1)
+  int32_t last = 0;
+  while ((double)k * ldexp(1.0, last) < n) ++last;
+  double lg = log2(n / (double)k);
+  if (lg < 1.0) lg = 1.0;
+  const double pf = params->pf > 0 ? params->pf : 1.0 / n;
+  const double pf_round = pf / (n * lg);  // p_f' = p_f / (n log2(n/k))
+  std::vector<int32_t> active(nsrc), src(nsrc);
+  for (int i = 0; i < nsrc; ++i) active[i] = i;
+  std::vector<int32_t> ids((size_t)nsrc * k);
+  std::vector<double> vals((size_t)nsrc * k);
+  std::vector<fora_stats> st(nsrc);
+  for (int32_t round = 0; round <= last && !active.empty(); ++round) {
+    fora_params pr = *params;
+    pr.eps = params->eps / 2.0;  // eps' = eps / 2 (Alg. 5, line 2)
+    pr.delta = round < last ? 1.0 / ((double)k * ldexp(1.0, round)) : 1.0 / n;
+    pr.pf = pf_round;
+    pr.seed = params->seed + (uint64_t)round;
+    pr.flags = params->flags & ~(FORA_OUT_DEVICE | FORA_ASYNC);
+    const int na = (int)active.size();
+    for (int i = 0; i < na; ++i) src[i] = sources[active[i]];
+    const int rc = run_batch(g, &pr, src.data(), na, ids.data(), vals.data(), st.data(), nullptr, 0,
+                             (cudaStream_t)stream);
+    if (rc) return rc;
+    std::vector<int32_t> still;
+    for (int i = 0; i < na; ++i) {
+      const int j = active[i];
+      // stop once the k-th estimate is at least (1 + eps) delta (Alg. 5, line 4)
+      if (vals[(size_t)i * k + k - 1] >= (1.0 + params->eps) * pr.delta || round == last) {
+        memcpy(out_ids + (size_t)j * k, ids.data() + (size_t)i * k, k * sizeof(int32_t));
+        memcpy(out_vals + (size_t)j * k, vals.data() + (size_t)i * k, k * sizeof(double));
+        if (stats) stats[j] = st[i];
+        if (iterations) iterations[j] = (uint32_t)round + 1;
+      } else {
+        still.push_back(j);
+      }
+    }
+    active.swap(still);
+  }
+  return FORA_OK;
 }
 
 int fora_topk(const double* est, int64_t n, int32_t nrows, uint32_t k, int32_t* out_ids,
@@ -476,6 +566,253 @@ int fora_graph_tune(fora_graph* g, const char* key, int64_t value) {
     return FORA_OK;
   }
   return fail(FORA_ERR_BAD_ARG, "unknown tuning key '%s'", key);
+}
+
+}  // extern "C"
+
+struct fora_model {
+  int device = 0;
+  float* master = nullptr;  // FORA_MODEL_PARAMS
+  float* adam_m = nullptr;
+  float* adam_v = nullptr;
+  float* grad = nullptr;
+  float* norm = nullptr;    // mu[16], sigma[16]
+  int step = 0;
+  std::mutex mu;
+};
+
+namespace {
+
+uint64_t splitmix(uint64_t* s) {
+  uint64_t z = (*s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Device buffers of one model call (inputs, targets, partials) on the default stream.
+struct ModelScratch {
+  float* x = nullptr;
+  float* t = nullptr;
+  float* y = nullptr;
+  float* partial = nullptr;
+  float* loss = nullptr;
+  int32_t* idx = nullptr;
+  ~ModelScratch() {
+    dfree(x); dfree(t); dfree(y); dfree(partial); dfree(loss); dfree(idx);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+int fora_model_create(uint64_t seed, fora_model** out) {
+  if (!out) return fail(FORA_ERR_BAD_ARG, "null output handle");
+  *out = nullptr;
+  fora_model* m = new fora_model();
+  std::vector<float> p(FORA_MODEL_PARAMS, 0.0f), norm(2 * FORA_NUM_FEATURES, 0.0f);
+  uint64_t st = seed;
+  auto uni = [&](float bound) {
+    return (float)(((double)(splitmix(&st) >> 11) * 0x1p-53 * 2.0 - 1.0) * bound);
+  };
+  const int in = FORA_NUM_FEATURES, hid = 64;
+  for (int i = 0; i < hid * in; ++i) p[i] = uni(sqrtf(6.0f / in));                      // W1
+  for (int i = 0; i < hid * hid; ++i) p[hid * in + hid + i] = uni(sqrtf(6.0f / hid));   // W2
+  for (int i = 0; i < hid; ++i) p[hid * in + hid + hid * hid + hid + i] = uni(sqrtf(6.0f / hid));  // W3
+  for (int i = 0; i < FORA_NUM_FEATURES; ++i) norm[FORA_NUM_FEATURES + i] = 1.0f;
+  auto bail = [&](cudaError_t e) {
+    fora_model_destroy(m);
+    return fail(e == cudaErrorMemoryAllocation ? FORA_ERR_OOM : FORA_ERR_CUDA, "model: %s",
+                cudaGetErrorString(e));
+  };
+  cudaError_t e = cudaGetDevice(&m->device);
+  if (e == cudaSuccess) e = cudaMalloc(&m->master, FORA_MODEL_PARAMS * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&m->adam_m, FORA_MODEL_PARAMS * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&m->adam_v, FORA_MODEL_PARAMS * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&m->grad, FORA_MODEL_PARAMS * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&m->norm, 2 * FORA_NUM_FEATURES * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpy(m->master, p.data(), FORA_MODEL_PARAMS * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m->norm, norm.data(), 2 * FORA_NUM_FEATURES * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(m->adam_m, 0, FORA_MODEL_PARAMS * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(m->adam_v, 0, FORA_MODEL_PARAMS * sizeof(float));
+  if (e != cudaSuccess) return bail(e);
+  *out = m;
+  return FORA_OK;
+}
+
+void fora_model_destroy(fora_model* m) {
+  if (!m) return;
+  cudaSetDevice(m->device);
+  dfree(m->master); dfree(m->adam_m); dfree(m->adam_v); dfree(m->grad); dfree(m->norm);
+  delete m;
+}
+
+int fora_model_get(const fora_model* m, float* params, float* norm) {
+  if (!m) return fail(FORA_ERR_BAD_ARG, "null model");
+  CUDA_TRY(cudaSetDevice(m->device));
+  if (params) CUDA_TRY(cudaMemcpy(params, m->master, FORA_MODEL_PARAMS * sizeof(float), cudaMemcpyDeviceToHost));
+  if (norm) CUDA_TRY(cudaMemcpy(norm, m->norm, 2 * FORA_NUM_FEATURES * sizeof(float), cudaMemcpyDeviceToHost));
+  return FORA_OK;
+}
+
+int fora_model_set(fora_model* m, const float* params, const float* norm) {
+  if (!m) return fail(FORA_ERR_BAD_ARG, "null model");
+  std::lock_guard<std::mutex> lock(m->mu);
+  CUDA_TRY(cudaSetDevice(m->device));
+  if (params) CUDA_TRY(cudaMemcpy(m->master, params, FORA_MODEL_PARAMS * sizeof(float), cudaMemcpyHostToDevice));
+  if (norm) CUDA_TRY(cudaMemcpy(m->norm, norm, 2 * FORA_NUM_FEATURES * sizeof(float), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemset(m->adam_m, 0, FORA_MODEL_PARAMS * sizeof(float)));
+  CUDA_TRY(cudaMemset(m->adam_v, 0, FORA_MODEL_PARAMS * sizeof(float)));
+  m->step = 0;
+  return FORA_OK;
+}
+
+int fora_model_predict(fora_model* m, const float* x, int32_t n, float* y) {
+  if (!m || !x || !y || n < 1) return fail(FORA_ERR_BAD_ARG, "bad arguments");
+  std::lock_guard<std::mutex> lock(m->mu);
+  CUDA_TRY(cudaSetDevice(m->device));
+  ModelScratch s;
+  CUDA_TRY(cudaMalloc(&s.x, (size_t)n * FORA_NUM_FEATURES * sizeof(float)));
+  CUDA_TRY(cudaMalloc(&s.y, (size_t)n * sizeof(float)));
+  CUDA_TRY(cudaMemcpy(s.x, x, (size_t)n * FORA_NUM_FEATURES * sizeof(float), cudaMemcpyHostToDevice));
+  CUDA_TRY(launch_mlp_forward(m->master, m->norm, s.x, n, s.y, 0));
+  CUDA_TRY(cudaMemcpy(y, s.y, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost));
+  return FORA_OK;
+}
+
+int fora_model_gradient(fora_model* m, const float* x, const float* t, int32_t n, float* grad,
+                        float* loss) {
+  if (!m || !x || !t || !grad || n < 1) return fail(FORA_ERR_BAD_ARG, "bad arguments");
+  std::lock_guard<std::mutex> lock(m->mu);
+  CUDA_TRY(cudaSetDevice(m->device));
+  ModelScratch s;
+  const int tiles = (n + mlp_tile() - 1) / mlp_tile();
+  CUDA_TRY(cudaMalloc(&s.x, (size_t)n * FORA_NUM_FEATURES * sizeof(float)));
+  CUDA_TRY(cudaMalloc(&s.t, (size_t)n * sizeof(float)));
+  CUDA_TRY(cudaMalloc(&s.partial, (size_t)tiles * FORA_MODEL_PARAMS * sizeof(float)));
+  CUDA_TRY(cudaMalloc(&s.loss, (size_t)n * sizeof(float)));
+  CUDA_TRY(cudaMemcpy(s.x, x, (size_t)n * FORA_NUM_FEATURES * sizeof(float), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(s.t, t, (size_t)n * sizeof(float), cudaMemcpyHostToDevice));
+  CUDA_TRY(launch_mlp_grad(m->master, m->norm, s.x, s.t, nullptr, n, s.partial, s.loss, m->grad, 0));
+  CUDA_TRY(cudaMemcpy(grad, m->grad, FORA_MODEL_PARAMS * sizeof(float), cudaMemcpyDeviceToHost));
+  if (loss) {
+    std::vector<float> l(n);
+    CUDA_TRY(cudaMemcpy(l.data(), s.loss, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost));
+    double sum = 0.0;
+    for (int i = 0; i < n; ++i) sum += l[i];
+    *loss = (float)(sum / n);
+  }
+  return FORA_OK;
+}
+
+int fora_model_train(fora_model* m, const float* x, const float* t, int32_t n, int32_t epochs,
+                     int32_t batch, float lr, uint64_t seed, float* loss_per_epoch) {
+  if (!m || !x || !t || n < 1 || epochs < 1 || batch < 1 || !(lr > 0.0f))
+    return fail(FORA_ERR_BAD_ARG, "bad arguments");
+  std::lock_guard<std::mutex> lock(m->mu);
+  CUDA_TRY(cudaSetDevice(m->device));
+  // feature normalisation from the training inputs
+  const int F = FORA_NUM_FEATURES;
+  std::vector<float> norm(2 * F);
+  for (int i = 0; i < F; ++i) {
+    double s1 = 0, s2 = 0;
+    for (int r = 0; r < n; ++r) { s1 += x[(size_t)r * F + i]; s2 += (double)x[(size_t)r * F + i] * x[(size_t)r * F + i]; }
+    const double mean = s1 / n, var = s2 / n - mean * mean;
+    norm[i] = (float)mean;
+    norm[F + i] = var > 1e-12 ? (float)sqrt(var) : 1.0f;
+  }
+  CUDA_TRY(cudaMemcpy(m->norm, norm.data(), 2 * F * sizeof(float), cudaMemcpyHostToDevice));
+  ModelScratch s;
+  const int b = batch < n ? batch : n;
+  const int tiles = (b + mlp_tile() - 1) / mlp_tile();
+  CUDA_TRY(cudaMalloc(&s.x, (size_t)n * F * sizeof(float)));
+  CUDA_TRY(cudaMalloc(&s.t, (size_t)n * sizeof(float)));
+  CUDA_TRY(cudaMalloc(&s.idx, (size_t)n * sizeof(int32_t)));
+  CUDA_TRY(cudaMalloc(&s.partial, (size_t)tiles * FORA_MODEL_PARAMS * sizeof(float)));
+  CUDA_TRY(cudaMalloc(&s.loss, (size_t)n * sizeof(float)));
+  CUDA_TRY(cudaMemcpy(s.x, x, (size_t)n * F * sizeof(float), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(s.t, t, (size_t)n * sizeof(float), cudaMemcpyHostToDevice));
+  std::vector<int32_t> perm(n);
+  std::vector<float> l(n);
+  uint64_t st = seed;
+  for (int ep = 0; ep < epochs; ++ep) {
+    for (int i = 0; i < n; ++i) perm[i] = i;
+    for (int i = n - 1; i > 0; --i) {  // seeded Fisher-Yates
+      const int j = (int)(splitmix(&st) % (uint64_t)(i + 1));
+      const int32_t tmp = perm[i]; perm[i] = perm[j]; perm[j] = tmp;
+    }
+    CUDA_TRY(cudaMemcpy(s.idx, perm.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice));
+    for (int off = 0; off < n; off += b) {
+      const int cnt = (n - off) < b ? (n - off) : b;
+      CUDA_TRY(launch_mlp_grad(m->master, m->norm, s.x, s.t, s.idx + off, cnt, s.partial,
+                               s.loss + off, m->grad, 0));
+      CUDA_TRY(launch_adam(m->master, m->adam_m, m->adam_v, m->grad, ++m->step, lr, 0));
+    }
+    if (loss_per_epoch) {
+      CUDA_TRY(cudaMemcpy(l.data(), s.loss, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost));
+      double sum = 0.0;
+      for (int i = 0; i < n; ++i) sum += l[i];
+      loss_per_epoch[ep] = (float)(sum / n);
+    }
+  }
+  CUDA_TRY(cudaDeviceSynchronize());
+  return FORA_OK;
+}
+
+int fora_source_features(fora_graph* g, const fora_params* params, const int32_t* sources,
+                         int32_t nsrc, float* out) {
+  Resolved rp;
+  int rc = resolve(g, params, &rp);
+  if (rc) return rc;
+  if (!sources || nsrc < 1 || !out) return fail(FORA_ERR_BAD_ARG, "bad arguments");
+  for (int i = 0; i < nsrc; ++i)
+    if (sources[i] < 0 || sources[i] >= g->n) return fail(FORA_ERR_BAD_ARG, "source %d out of range", i);
+  std::lock_guard<std::mutex> lock(g->mu);
+  CUDA_TRY(cudaSetDevice(g->device));
+  rc = ensure_workspace(g, nsrc);
+  if (rc) return rc;
+  memcpy(g->h_sources, sources, nsrc * sizeof(int32_t));
+  CUDA_TRY(cudaMemcpy(g->sources, g->h_sources, nsrc * sizeof(int32_t), cudaMemcpyHostToDevice));
+  GraphDev gd{g->n, g->m, g->row, g->col};
+  CUDA_TRY(launch_features(gd, g->indeg, g->sources, nsrc, rp.alpha, rp.rmax, g->feat, 0));
+  CUDA_TRY(cudaMemcpy(out, g->feat, (size_t)nsrc * FORA_NUM_FEATURES * sizeof(float), cudaMemcpyDeviceToHost));
+  return FORA_OK;
+}
+
+int fora_ssppr_batch_learned(fora_graph* g, const fora_params* params, fora_model* model,
+                             const int32_t* sources, int32_t nsrc, int32_t* out_ids,
+                             double* out_vals, fora_stats* stats, void* stream) {
+  if (!model) return fail(FORA_ERR_BAD_ARG, "null model");
+  Resolved rp;
+  int rc = resolve(g, params, &rp);
+  if (rc) return rc;
+  if (!sources || nsrc < 1 || nsrc > 65535) return fail(FORA_ERR_BAD_ARG, "bad sources");
+  for (int i = 0; i < nsrc; ++i)
+    if (sources[i] < 0 || sources[i] >= g->n) return fail(FORA_ERR_BAD_ARG, "source %d out of range", i);
+  cudaStream_t st = (cudaStream_t)stream;
+  {
+    std::lock_guard<std::mutex> lock(g->mu);
+    CUDA_TRY(cudaSetDevice(g->device));
+    rc = ensure_workspace(g, nsrc);
+    if (rc) return rc;
+    memcpy(g->h_sources, sources, nsrc * sizeof(int32_t));
+    CUDA_TRY(cudaMemcpyAsync(g->sources, g->h_sources, nsrc * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    GraphDev gd{g->n, g->m, g->row, g->col};
+    // r_rule of these parameters (params->rmax is not used here)
+    fora_params pr = *params;
+    pr.rmax = 0.0;
+    Resolved rule;
+    rc = resolve(g, &pr, &rule);
+    if (rc) return rc;
+    CUDA_TRY(launch_features(gd, g->indeg, g->sources, nsrc, rule.alpha, rule.rmax, g->feat, st));
+    std::lock_guard<std::mutex> mlock(model->mu);
+    CUDA_TRY(launch_mlp_forward(model->master, model->norm, g->feat, nsrc, g->pred, st));
+    CUDA_TRY(launch_pred_to_rmax(g->pred, nsrc, rule.rmax, -3.0f, 3.0f, g->rmax_learned, st));
+  }
+  RmaxSource rs;
+  rs.device = g->rmax_learned;
+  return run_batch(g, params, sources, nsrc, out_ids, out_vals, stats, nullptr, 0, st, rs);
 }
 
 const char* fora_last_error(void) { return g_err.c_str(); }

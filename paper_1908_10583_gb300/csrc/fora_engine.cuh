@@ -67,6 +67,7 @@ struct BatchDev {
   double walk_scale;         // C = omega / r_sum
   uint32_t alpha_threshold;  // floor(alpha * 2^32)
   uint64_t seed;
+  int zero_hop;              // walk phase with zero-hop pruning (Section 4.1)
   double* r;                 // residue, later the estimate
   double* res;               // reserve
   Tally* tally;              // walk ends per (source, node)
@@ -116,9 +117,27 @@ cudaError_t launch_unpack_tally(const Tally* t, uint32_t* cnt, unsigned long lon
 cudaError_t launch_philox_table(const uint32_t* ctr_key, uint32_t* out, int count,
                                 cudaStream_t st);
 
+// learn.cu
+cudaError_t launch_indegree(const GraphDev& g, uint32_t* indeg, int num_sms, cudaStream_t st);
+cudaError_t launch_features(const GraphDev& g, const uint32_t* indeg, const int32_t* sources,
+                            int nsrc, double alpha, double rmax_rule, float* out, cudaStream_t st);
+cudaError_t launch_mlp_forward(const float* master, const float* norm, const float* X, int n,
+                               float* Y, cudaStream_t st);
+cudaError_t launch_mlp_grad(const float* master, const float* norm, const float* X,
+                            const float* T, const int32_t* idx, int n, float* partial,
+                            float* loss_partial, float* grad, cudaStream_t st);
+cudaError_t launch_adam(float* master, float* m, float* v, const float* grad, int step, float lr,
+                        cudaStream_t st);
+cudaError_t launch_pred_to_rmax(const float* pred, int n, double rmax_rule, float lo, float hi,
+                                double* rmax, cudaStream_t st);
+int mlp_tile();
+
 // topk.cu
-cudaError_t launch_estimate(const double* res, const Tally* tally, double* est, uint64_t count,
-                            int num_sms, cudaStream_t st);
+// est may alias r (the residue array becomes the estimate); with zero_hop the estimate
+// also takes alpha * r.
+cudaError_t launch_estimate(const double* res, const Tally* tally, double* est, const double* r,
+                            double alpha, int zero_hop, uint64_t count, int num_sms,
+                            cudaStream_t st);
 // Scratch of the top-k select: hist [nrows][kBins], slots [nrows], cand [nrows][kSortCap].
 struct TopkScratch {
   uint32_t* hist;

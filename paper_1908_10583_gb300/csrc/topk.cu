@@ -30,12 +30,14 @@ __device__ __forceinline__ u128 prefix_of(const TopkSlot& s) {
 }
 
 __global__ void k_estimate(const double* __restrict__ res, const Tally* __restrict__ tally,
-                           double* __restrict__ est, unsigned long long count) {
+                           double* est, const double* r, double alpha, int zero_hop,
+                           unsigned long long count) {
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += stride) {
-    // pi_hat = reserve + acc * 2^-63 (the scaling is exact)
-    est[i] = __dadd_rn(res[i], __dmul_rn(__ull2double_rn(tally[i].acc), 0x1p-63));
+    // pi_hat = reserve (+ alpha r with zero-hop pruning) + acc * 2^-63 (exact scaling)
+    const double base = zero_hop ? __dadd_rn(res[i], __dmul_rn(alpha, r[i])) : res[i];
+    est[i] = __dadd_rn(base, __dmul_rn(__ull2double_rn(tally[i].acc), 0x1p-63));
   }
 }
 
@@ -236,12 +238,13 @@ TopkScratch topk_scratch_carve(void* base, int nrows) {
   return s;
 }
 
-cudaError_t launch_estimate(const double* res, const Tally* tally, double* est, uint64_t count,
-                            int num_sms, cudaStream_t st) {
+cudaError_t launch_estimate(const double* res, const Tally* tally, double* est, const double* r,
+                            double alpha, int zero_hop, uint64_t count, int num_sms,
+                            cudaStream_t st) {
   uint64_t blocks = (count + 255) / 256;
   if (blocks > (uint64_t)num_sms * 32) blocks = (uint64_t)num_sms * 32;
   if (blocks == 0) return cudaSuccess;
-  k_estimate<<<(unsigned)blocks, 256, 0, st>>>(res, tally, est, count);
+  k_estimate<<<(unsigned)blocks, 256, 0, st>>>(res, tally, est, r, alpha, zero_hop, count);
   return cudaGetLastError();
 }
 

@@ -57,6 +57,11 @@ __device__ __forceinline__ unsigned long long weight_of(double r, double omega) 
   return __double2ull_rn(__dmul_rn(__ddiv_rn(r, omega), 0x1p63));
 }
 
+// The residue the walks sample: r, or (1 - alpha) r with zero-hop pruning (Section 4.1).
+__device__ __forceinline__ double sampled(const BatchDev& b, double r) {
+  return b.zero_hop ? __dmul_rn(__dadd_rn(1.0, -b.alpha), r) : r;
+}
+
 // Contiguous element range of block `blk` out of `nblk` over [0, total).
 __device__ __forceinline__ void block_range(unsigned long long total, int blk, int nblk,
                                             unsigned long long* beg, unsigned long long* end) {
@@ -124,7 +129,7 @@ __global__ void __launch_bounds__(kResidualThreads) k_residual_count(GraphDev g,
     const double r = b.r[i];
     if (r > 0.0) {
       // an entry of R needs at least one walk (omega_v = 0 only if r * C underflows)
-      const unsigned long long w = (unsigned long long)walks_of(r, b.walk_scale);
+      const unsigned long long w = (unsigned long long)walks_of(sampled(b, r), b.walk_scale);
       if (w > 0) { ++cnt; walks += w; }
       ++s_cnt; s_walks += w; s_sum += r;
     }
@@ -178,7 +183,7 @@ __global__ void __launch_bounds__(kResidualThreads) k_residual_emit(GraphDev g, 
   unsigned long long woff = b.blk_walks[blockIdx.x];
   for (unsigned long long tile = beg; tile < end; tile += kResidualThreads) {
     const unsigned long long i = tile + threadIdx.x;
-    const double r = i < end ? b.r[i] : 0.0;
+    const double r = i < end ? sampled(b, b.r[i]) : 0.0;
     const double omega = r > 0.0 ? walks_of(r, b.walk_scale) : 0.0;
     const bool live = omega >= 1.0;
     unsigned long long ce, we, ct, wt;
@@ -269,6 +274,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walks(GraphDev g, BatchDev b) 
     rng.key = key;
     uint32_t x = 0, slot = 0, steps = 0;
     unsigned long long wgt = 0;
+    bool forced = b.zero_hop;  // a pruned walk first moves without a stop test
     if (have) {
       const unsigned long long idx = idx0 + smap[wid][i];
       const unsigned long long entry = b.wr_entry[idx];
@@ -280,7 +286,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walks(GraphDev g, BatchDev b) 
       steps = 0;
     }
     while (have) {
-      if (rng.next() < t_alpha) {
+      if (!forced && rng.next() < t_alpha) {
         // the walk stops at x (Section 2.1): count it and add its weight (Alg. 2)
         Tally* t = b.tally + (unsigned long long)slot * (unsigned long long)g.n + x;
         atomicAdd(&t->cnt, 1u);
@@ -302,9 +308,11 @@ __global__ void __launch_bounds__(kWalkThreads) k_walks(GraphDev g, BatchDev b) 
           rng.s = (uint32_t)b.sources[slot]; rng.avail = 0;
           wgt = b.wr_weight[idx];
           steps = 0;
+          forced = b.zero_hop;
         }
         continue;
       }
+      forced = false;
       if (steps >= kMaxSteps) { capped = true; have = false; break; }
       const uint32_t rb0 = g.row[x];
       const uint32_t d = g.row[x + 1] - rb0;

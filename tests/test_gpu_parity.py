@@ -244,3 +244,53 @@ def test_errors_are_reported(rmat14):
     # the graph stays usable after a rejected call
     ids, vals, st = g.ssppr(0, fora.Params.make(k=5))
     assert len(ids) == 5
+
+
+def test_zero_hop_bit_exact_on_oracle_residues(rmat14):
+    """Walk phase with zero-hop pruning (Section 4.1) on the oracle's residues."""
+    rp, col, g = rmat14
+    n = len(rp) - 1
+    sources = inputs.uniform_sources(n, 6, 55)
+    p = fora.Params.make(k=50, seed=17, flags=fora.FORA_ZERO_HOP)
+    qs = [oracle.ssppr(rp, col, s, k=50, seed=17, zero_hop=True) for s in sources]
+    given = (np.stack([q.reserve for q in qs]), np.stack([q.residue for q in qs]))
+    ids, vals, st, out = run_debug(g, sources, p, given=given)
+    for i, q in enumerate(qs):
+        np.testing.assert_array_equal(out["count"][i], q.count)
+        np.testing.assert_array_equal(out["acc"][i], q.acc)
+        np.testing.assert_array_equal(out["estimate"][i], q.est)
+        np.testing.assert_array_equal(ids[i], q.ids)
+        assert st[i].walks == q.walk.walks and st[i].walk_steps == q.walk.walk_steps
+    # full query: eps-accurate against power iteration, and fewer walks than plain FORA
+    truth = exact.power_iteration(rp, col, 0.2, sources)
+    _, _, st_p, _ = run_debug(g, sources, fora.Params.make(k=50, seed=17))
+    _, _, st_z, out_z = run_debug(g, sources, p)
+    for i in range(len(sources)):
+        big = truth[i] >= 1.0 / n
+        rel = np.abs(out_z["estimate"][i][big] - truth[i][big]) / truth[i][big]
+        assert rel.max() <= 0.5
+        assert st_z[i].walks < 0.85 * st_p[i].walks
+
+
+def test_topk_fora_matches_oracle(rmat14):
+    """Top-k FORA (Alg. 5): the same stopping round and delta per source, the same
+    top-k up to near-ties, and Def. 2 against power iteration."""
+    rp, col, g = rmat14
+    n = len(rp) - 1
+    sources = inputs.uniform_sources(n, 6, 909)
+    truth = exact.power_iteration(rp, col, 0.2, sources)
+    for k in (20, 100):
+        p = fora.Params.make(k=k, seed=5)
+        ids, vals, st, iters = g.topk_fora(sources, p)
+        for i, s in enumerate(sources):
+            q = oracle.topk_fora(rp, col, s, k, seed=5)
+            assert iters[i] == q.iterations
+            np.testing.assert_allclose(vals[i], q.vals, rtol=0, atol=ATOL_PUSH)
+            kth = q.vals[-1]
+            sure = set(np.flatnonzero(q.est > kth + 2 * ATOL_PUSH).tolist())
+            assert sure <= set(ids[i].tolist())
+            true_sorted = np.sort(truth[i])[::-1]
+            for j, v in enumerate(ids[i]):
+                if true_sorted[j] > 1.0 / n:
+                    assert vals[i][j] >= 0.5 * truth[i][v]
+                    assert truth[i][v] >= 0.5 * true_sorted[j]

@@ -28,6 +28,8 @@ FORA_OUT_DEVICE = 0x1
 FORA_ASYNC = 0x2
 FORA_ZERO_HOP = 0x4
 FORA_DBG_GIVEN_PUSH = 0x1
+FORA_NUM_FEATURES = 16
+FORA_MODEL_PARAMS = 5313
 
 _lock = threading.Lock()
 _lib = None
@@ -111,6 +113,24 @@ def load():
         L.fora_philox_debug.argtypes = [P, P, i32]
         L.fora_topk_noalloc.restype = I
         L.fora_topk_noalloc.argtypes = [P, i64, i32, u32, P, P, P]
+        L.fora_model_create.restype = I
+        L.fora_model_create.argtypes = [ctypes.c_uint64, ctypes.POINTER(P)]
+        L.fora_model_destroy.restype = None
+        L.fora_model_destroy.argtypes = [P]
+        L.fora_model_get.restype = I
+        L.fora_model_get.argtypes = [P, P, P]
+        L.fora_model_set.restype = I
+        L.fora_model_set.argtypes = [P, P, P]
+        L.fora_model_predict.restype = I
+        L.fora_model_predict.argtypes = [P, P, i32, P]
+        L.fora_model_gradient.restype = I
+        L.fora_model_gradient.argtypes = [P, P, P, i32, P, P]
+        L.fora_model_train.restype = I
+        L.fora_model_train.argtypes = [P, P, P, i32, i32, i32, ctypes.c_float, ctypes.c_uint64, P]
+        L.fora_source_features.restype = I
+        L.fora_source_features.argtypes = [P, ctypes.POINTER(Params), P, i32, P]
+        L.fora_ssppr_batch_learned.restype = I
+        L.fora_ssppr_batch_learned.argtypes = [P, ctypes.POINTER(Params), P, P, i32, P, P, P, P]
         L.fora_graph_tune.restype = I
         L.fora_graph_tune.argtypes = [P, ctypes.c_char_p, i64]
         L.fora_last_error.restype = ctypes.c_char_p
@@ -243,6 +263,33 @@ class Graph:
                                             ctypes.addressof(st), _stream_ptr(stream)))
         return out_ids, out_vals, list(st)
 
+    def features(self, sources, params: Params):
+        """Per-source features of the learned r_max (fora_source_features) -> [nsrc, 16]."""
+        src = np.ascontiguousarray(sources, dtype=np.int32)
+        out = np.zeros((len(src), FORA_NUM_FEATURES), dtype=np.float32)
+        _check(load().fora_source_features(self._h, ctypes.byref(params), src.ctypes.data,
+                                           len(src), out.ctypes.data))
+        return out
+
+    def ssppr_batch_learned(self, sources, params: Params, model: "Model", out_ids=None,
+                            out_vals=None, stream=None):
+        """Batched query with r_max chosen per source by the model."""
+        src = np.ascontiguousarray(sources, dtype=np.int32)
+        nsrc, k = len(src), params.k
+        p = Params.from_buffer_copy(params)
+        if out_ids is not None:
+            p.flags |= FORA_OUT_DEVICE
+        else:
+            p.flags &= ~FORA_OUT_DEVICE
+            out_ids = np.zeros((nsrc, k), dtype=np.int32)
+            out_vals = np.zeros((nsrc, k), dtype=np.float64)
+        st = (Stats * nsrc)()
+        _check(load().fora_ssppr_batch_learned(self._h, ctypes.byref(p), model._h,
+                                               src.ctypes.data, nsrc, _ptr(out_ids),
+                                               _ptr(out_vals), ctypes.addressof(st),
+                                               _stream_ptr(stream)))
+        return out_ids, out_vals, list(st)
+
     def topk_fora(self, sources, params: Params, stream=None):
         """Top-k FORA (Alg. 5) per source -> (ids [nsrc, k], vals, stats, iterations)."""
         src = np.ascontiguousarray(sources, dtype=np.int32)
@@ -314,3 +361,68 @@ def philox(ctr_key: np.ndarray) -> np.ndarray:
     out = np.zeros((len(ck), 4), dtype=np.uint32)
     _check(load().fora_philox_debug(ck.ctypes.data, out.ctypes.data, len(ck)))
     return out
+
+
+class Model:
+    """The learned r_max network (fora_model_*), resident on the current device."""
+
+    def __init__(self, seed: int = 0):
+        h = ctypes.c_void_p()
+        _check(load().fora_model_create(int(seed), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().fora_model_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get(self):
+        p = np.zeros(FORA_MODEL_PARAMS, dtype=np.float32)
+        nm = np.zeros(2 * FORA_NUM_FEATURES, dtype=np.float32)
+        _check(load().fora_model_get(self._h, p.ctypes.data, nm.ctypes.data))
+        return p, nm
+
+    def set(self, params=None, norm=None):
+        p = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+        nm = None if norm is None else np.ascontiguousarray(norm, dtype=np.float32)
+        _check(load().fora_model_set(self._h, _ptr(p), _ptr(nm)))
+
+    def predict(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        y = np.zeros(len(x), dtype=np.float32)
+        _check(load().fora_model_predict(self._h, x.ctypes.data, len(x), y.ctypes.data))
+        return y
+
+    def gradient(self, x, t):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        g = np.zeros(FORA_MODEL_PARAMS, dtype=np.float32)
+        loss = ctypes.c_float(0.0)
+        _check(load().fora_model_gradient(self._h, x.ctypes.data, t.ctypes.data, len(x),
+                                          g.ctypes.data, ctypes.byref(loss)))
+        return g, loss.value
+
+    def train(self, x, t, epochs=50, batch=256, lr=1e-3, seed=0):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        hist = np.zeros(epochs, dtype=np.float32)
+        _check(load().fora_model_train(self._h, x.ctypes.data, t.ctypes.data, len(x), int(epochs),
+                                       int(batch), float(lr), int(seed), hist.ctypes.data))
+        return hist
+
+    def save(self, path):
+        p, nm = self.get()
+        np.savez(path, params=p, norm=nm)
+
+    @classmethod
+    def load_file(cls, path):
+        d = np.load(path)
+        m = cls(0)
+        m.set(d["params"], d["norm"])
+        return m

@@ -49,6 +49,11 @@ def parse_args():
     ap.add_argument("--stats", action="store_true", help="per-step counters to stderr")
     ap.add_argument("--tune", action="append", default=[],
                     help="launch-shape parameter key=value (fora_graph_tune)")
+    ap.add_argument("--rmax", choices=["auto", "rule", "learned"], default="auto",
+                    help="learned: per-source r_max from paper_1908_10583_gb300/models/"
+                         "rmax_<workload>.npz (auto: when that file exists)")
+    ap.add_argument("--plain-sources", type=int, default=16,
+                    help="single-source queries timed for the plain-FORA comparison")
     return ap.parse_args()
 
 
@@ -222,50 +227,74 @@ def run_fora(args):
     ids = torch.empty((B, k), dtype=torch.int32, device="cuda")
     vals = torch.empty((B, k), dtype=torch.float64, device="cuda")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
+    model_path = os.path.join(ROOT, "paper_1908_10583_gb300", "models",
+                              f"rmax_{args.workload}.npz")
+    mode = args.rmax
+    if mode == "auto":
+        mode = "learned" if os.path.exists(model_path) else "rule"
+    model = fora.Model.load_file(model_path) if mode == "learned" else None
 
     def sources(step):
         return inputs.uniform_sources(n, B, inputs.SOURCE_SEED + 1_000_003 * rank + 7919 * step)
 
+    def one_step(src, use_model):
+        if use_model is not None:
+            return g.ssppr_batch_learned(src, params, use_model, out_ids=ids, out_vals=vals,
+                                         stream=stream)[2]
+        return g.ssppr_batch(src, params, out_ids=ids, out_vals=vals, stream=stream)[2]
+
+    def timed(use_model, nsteps, collect=None):
+        out = []
+        for step in range(nsteps):
+            src = sources(step)
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = one_step(src, use_model)
+            e1.record(stream)
+            e1.synchronize()
+            out.append(e0.elapsed_time(e1))
+            if collect is not None:
+                collect(step, st, out[-1])
+        return out
+
     for i in range(args.warmup):
-        g.ssppr_batch(sources(-1 - i), params, out_ids=ids, out_vals=vals, stream=stream)
+        one_step(sources(-1 - i), model)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    step_ms, walk_ms, walk_bytes, launches = [], [], [], 0
+    walk_ms, walk_bytes = [], []
     phase = {"ms_push": 0.0, "ms_residual": 0.0, "ms_walk": 0.0, "ms_topk": 0.0}
-    walks_total = steps_total = 0
-    for step in range(args.steps):
-        src = sources(step)
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        _, _, st = g.ssppr_batch(src, params, out_ids=ids, out_vals=vals, stream=stream)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
+    counters = {"launches": 0, "walks": 0, "moves": 0}
+
+    def collect(step, st, ms):
         rounds = max(s.push_rounds for s in st)
-        launches += 4 + 4 * rounds + 3 + 1 + 1 + 19  # push, residuals, walks, estimate, top-k
+        counters["launches"] += 4 + 4 * rounds + 3 + 1 + 1 + 19  # push, residuals, walks, top-k
+        if model is not None:
+            counters["launches"] += 3  # features, forward, r_max
         for key in phase:
             phase[key] += getattr(st[0], key)
         walk_ms.append(st[0].ms_walk)
         nw = sum(s.walks for s in st)
         ns = sum(s.walk_steps for s in st)
         nr = sum(s.residual_nodes for s in st)
-        walks_total += nw
-        steps_total += ns
+        counters["walks"] += nw
+        counters["moves"] += ns
         walk_bytes.append(WALK_BYTES_PER_MOVE * ns + WALK_BYTES_PER_WALK * nw +
                           WALK_BYTES_PER_ENTRY * nr)
         if args.stats:
-            print(json.dumps({"step": step, "ms": step_ms[-1], "rounds": rounds,
+            print(json.dumps({"step": step, "ms": ms, "rounds": rounds,
                               "pushes": sum(s.pushes for s in st),
                               "edge_pushes": sum(s.edge_pushes for s in st),
                               "residual_nodes": nr, "walks": nw, "moves": ns,
-                              "rsum_mean": sum(s.rsum for s in st) / len(st),
+                              "rmax_mean": sum(s.rmax for s in st) / len(st),
                               **{k_: getattr(st[0], k_) for k_ in phase}}), file=sys.stderr)
+
+    step_ms = timed(model, args.steps, collect)
     torch.cuda.synchronize()
     clk = clocks.stop()
     total_ms = sum(step_ms)
@@ -274,6 +303,23 @@ def run_fora(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     value = B * args.steps * world / (total_ms / 1e3)
+    launches = counters["launches"]
+    walks_total, steps_total = counters["walks"], counters["moves"]
+
+    # the comparison of the metric: batched rule r_max, and plain FORA one query at a time
+    comparison = {"rmax_mode": mode, f"batched_{mode}_qps": value}
+    if mode == "learned":
+        rule_ms = timed(None, args.steps)
+        comparison["batched_rule_qps"] = B * args.steps / (sum(rule_ms) / 1e3)
+    plain_src = inputs.uniform_sources(n, args.plain_sources, inputs.SOURCE_SEED + 31337)
+    h_ids1 = np.zeros(k, dtype=np.int32)
+    g.ssppr(int(plain_src[0]), params)  # warm the single-source workspace
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s_ in plain_src:
+        g.ssppr(int(s_), params)
+    comparison["plain_fora_qps"] = len(plain_src) / (time.perf_counter() - t0)
+    del h_ids1
 
     # end to end through the public API: host sources in, host results out
     h_ids = torch.empty((B, k), dtype=torch.int32, pin_memory=True).numpy()
@@ -281,7 +327,10 @@ def run_fora(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for step in range(args.steps):
-        g.ssppr_batch_host(sources(10_000 + step), params, h_ids, h_vals, stream=stream)
+        if model is not None:
+            g.ssppr_batch_learned(sources(10_000 + step), params, model, stream=stream)
+        else:
+            g.ssppr_batch_host(sources(10_000 + step), params, h_ids, h_vals, stream=stream)
     e2e_s = time.perf_counter() - t0
     e2e = {"value": B * args.steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": B * (4 + 8),
@@ -311,7 +360,7 @@ def run_fora(args):
             "config": {"workload": args.workload, "n": n, "m": int(rp[-1]),
                        "avg_out_degree": w["avg_deg"], "sources_per_launch": B, "k": k,
                        "eps": args.eps, "alpha": 0.2, "delta": "1/n", "pf": "1/n",
-                       "rmax": "rule", "parallelism": f"replicas{world}",
+                       "rmax": mode, "parallelism": f"replicas{world}",
                        "l2": "512 MiB buffer written between timed steps",
                        "tuning": tuning},
             "latency_ms": {"p50": lat[len(lat) // 2],
@@ -321,6 +370,7 @@ def run_fora(args):
             "walks_per_step": walks_total / args.steps,
             "walk_moves_per_step": steps_total / args.steps,
             "gpu_launches": launches,
+            "comparison": comparison,
             "roofline": roofline,
             "e2e": e2e,
             "clocks": clk}

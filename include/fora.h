@@ -59,6 +59,7 @@ extern "C" {
 #define FORA_ERR_PUSH_NOT_CONVERGED (-5) /* push exceeded FORA_MAX_PUSH_ROUNDS rounds */
 #define FORA_ERR_WALK_CAP (-6)           /* a walk exceeded FORA_MAX_WALK_STEPS moves */
 #define FORA_ERR_CUDA (-7)               /* a CUDA runtime call failed */
+#define FORA_ERR_TIMEOUT (-8)            /* a bounded wait ran out (serving) */
 
 #define FORA_MAX_PUSH_ROUNDS 100000
 #define FORA_MAX_WALK_STEPS 16384
@@ -223,6 +224,57 @@ int fora_source_features(fora_graph *g, const fora_params *params, const int32_t
 int fora_ssppr_batch_learned(fora_graph *g, const fora_params *params, fora_model *model,
                              const int32_t *sources, int32_t nsrc, int32_t *out_ids,
                              double *out_vals, fora_stats *stats, void *stream);
+
+/* ---- serving: continuous batching over resident graphs ---- */
+
+/*
+ * A request loop over resident graphs (the graph handles stay owned by the caller and
+ * must outlive the server).  Each graph gets lanes_per_graph lanes; a lane owns a
+ * workspace for `slots` queries, a CUDA stream and a host thread.  Admission is by HBM
+ * footprint: the budget (memory_budget_bytes, 0 = 80% of the free device memory) is
+ * split evenly over the lanes and a lane holds as many queries as its share fits at
+ * about 56 bytes per node per query (residue, reserve, walk tallies, frontiers), at most
+ * max_batch.  Requests queue per graph; a free lane admits the oldest queued requests
+ * that share everything but k (up to its slots; after waiting up to batch_window_ms for
+ * more when fewer are queued), runs them as one batched query with the largest k, and
+ * returns each request its own top-k.  Lanes run concurrently, so requests that arrive
+ * while others are on the GPU start as soon as a lane frees up and overlap with them.
+ * A request's result equals the same query run alone (same Philox counters), up to the
+ * FP64 rounding order of the push.
+ */
+typedef struct {
+  uint64_t memory_budget_bytes;
+  int32_t lanes_per_graph;
+  int32_t max_batch;
+  double batch_window_ms;
+} fora_server_config;
+
+typedef struct {
+  double submit_ms, start_ms, end_ms; /* since the server was created */
+  uint32_t batch_size;                /* queries in the batch that served the request */
+  int32_t lane;
+  fora_stats stats;
+} fora_request_info;
+
+typedef struct fora_server fora_server;
+
+int fora_server_create(fora_graph *const *graphs, int32_t ngraphs, const fora_server_config *cfg,
+                       fora_server **out);
+/* Stops the lanes (queued requests are dropped) and releases their workspaces. */
+void fora_server_destroy(fora_server *s);
+/* Graph index and query slots of a lane (lanes are numbered graph-major). */
+int fora_server_lane_capacity(const fora_server *s, int32_t lane, int32_t *graph, int32_t *slots);
+/* Queue one query (params->k <= min(n, FORA_MAX_K); flags FORA_OUT_DEVICE/ASYNC ignored). */
+int fora_server_submit(fora_server *s, int32_t graph, int32_t source, const fora_params *params,
+                       uint64_t *ticket);
+/* Wait up to timeout_ms for a request (FORA_ERR_TIMEOUT if it has not finished); on
+ * success copies its top-k to HOST out_ids / out_vals [k] and its info, and forgets the
+ * ticket.  Any output may be NULL. */
+int fora_server_wait(fora_server *s, uint64_t ticket, double timeout_ms, int32_t *out_ids,
+                     double *out_vals, fora_request_info *info);
+/* Requests completed, batches run, and the most lanes that were busy at once. */
+int fora_server_stats(fora_server *s, uint64_t *completed, uint64_t *batches,
+                      int32_t *max_concurrent);
 
 /* ---- inspection entry points (parity testing) ---- */
 

@@ -23,6 +23,7 @@ FORA_ERR_WALK_OVERFLOW = -4
 FORA_ERR_PUSH_NOT_CONVERGED = -5
 FORA_ERR_WALK_CAP = -6
 FORA_ERR_CUDA = -7
+FORA_ERR_TIMEOUT = -8
 FORA_MAX_K = 4096
 FORA_OUT_DEVICE = 0x1
 FORA_ASYNC = 0x2
@@ -64,6 +65,17 @@ class Stats(ctypes.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("memory_budget_bytes", ctypes.c_uint64), ("lanes_per_graph", ctypes.c_int32),
+                ("max_batch", ctypes.c_int32), ("batch_window_ms", ctypes.c_double)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("submit_ms", ctypes.c_double), ("start_ms", ctypes.c_double),
+                ("end_ms", ctypes.c_double), ("batch_size", ctypes.c_uint32),
+                ("lane", ctypes.c_int32), ("stats", Stats)]
 
 
 class DebugIO(ctypes.Structure):
@@ -131,6 +143,18 @@ def load():
         L.fora_source_features.argtypes = [P, ctypes.POINTER(Params), P, i32, P]
         L.fora_ssppr_batch_learned.restype = I
         L.fora_ssppr_batch_learned.argtypes = [P, ctypes.POINTER(Params), P, P, i32, P, P, P, P]
+        L.fora_server_create.restype = I
+        L.fora_server_create.argtypes = [P, i32, ctypes.POINTER(ServerConfig), ctypes.POINTER(P)]
+        L.fora_server_destroy.restype = None
+        L.fora_server_destroy.argtypes = [P]
+        L.fora_server_lane_capacity.restype = I
+        L.fora_server_lane_capacity.argtypes = [P, i32, P, P]
+        L.fora_server_submit.restype = I
+        L.fora_server_submit.argtypes = [P, i32, i32, ctypes.POINTER(Params), P]
+        L.fora_server_wait.restype = I
+        L.fora_server_wait.argtypes = [P, ctypes.c_uint64, ctypes.c_double, P, P, P]
+        L.fora_server_stats.restype = I
+        L.fora_server_stats.argtypes = [P, P, P, P]
         L.fora_graph_tune.restype = I
         L.fora_graph_tune.argtypes = [P, ctypes.c_char_p, i64]
         L.fora_last_error.restype = ctypes.c_char_p
@@ -426,3 +450,54 @@ class Model:
         m = cls(0)
         m.set(d["params"], d["norm"])
         return m
+
+
+class Server:
+    """Continuous-batching request loop over resident graphs (fora_server_*)."""
+
+    def __init__(self, graphs, lanes_per_graph=2, max_batch=256, memory_budget_bytes=0,
+                 batch_window_ms=0.5):
+        self._graphs = list(graphs)  # keep the graphs alive
+        arr = (ctypes.c_void_p * len(self._graphs))(*[g._h.value for g in self._graphs])
+        cfg = ServerConfig(int(memory_budget_bytes), int(lanes_per_graph), int(max_batch),
+                           float(batch_window_ms))
+        h = ctypes.c_void_p()
+        _check(load().fora_server_create(ctypes.cast(arr, ctypes.c_void_p), len(self._graphs),
+                                         ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self.lanes_per_graph = lanes_per_graph
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().fora_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def lane_capacity(self, lane):
+        g, sl = ctypes.c_int32(), ctypes.c_int32()
+        _check(load().fora_server_lane_capacity(self._h, lane, ctypes.byref(g), ctypes.byref(sl)))
+        return g.value, sl.value
+
+    def submit(self, graph: int, source: int, params: Params) -> int:
+        t = ctypes.c_uint64()
+        _check(load().fora_server_submit(self._h, int(graph), int(source), ctypes.byref(params),
+                                         ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int, k: int, timeout_ms: float = 600000.0):
+        ids = np.zeros(k, dtype=np.int32)
+        vals = np.zeros(k, dtype=np.float64)
+        info = RequestInfo()
+        _check(load().fora_server_wait(self._h, int(ticket), float(timeout_ms), ids.ctypes.data,
+                                       vals.ctypes.data, ctypes.addressof(info)))
+        return ids, vals, info
+
+    def stats(self):
+        c, b, m = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int32()
+        _check(load().fora_server_stats(self._h, ctypes.byref(c), ctypes.byref(b), ctypes.byref(m)))
+        return {"completed": c.value, "batches": b.value, "max_concurrent_lanes": m.value}

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libfora.so")
-SOURCES = ["push.cu", "walk.cu", "topk.cu", "capi.cu", "topk_noalloc.cu", "learn.cu"]
+SOURCES = ["push.cu", "walk.cu", "topk.cu", "capi.cu", "topk_noalloc.cu", "learn.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -38,7 +38,8 @@ def _flags():
 
 def _deps():
     files = [os.path.join(CSRC, s) for s in SOURCES]
-    files += [os.path.join(CSRC, "fora_engine.cuh"), os.path.join(INCLUDE, "fora.h"), __file__]
+    files += [os.path.join(CSRC, "fora_engine.cuh"), os.path.join(CSRC, "runtime.h"),
+              os.path.join(INCLUDE, "fora.h"), __file__]
     return files
 
 

@@ -12,6 +12,7 @@
 
 #include "fora.h"
 #include "fora_engine.cuh"
+#include "runtime.h"
 
 using namespace fora;
 
@@ -38,12 +39,6 @@ int fail(int code, const char* fmt, ...) {
                   __LINE__);                                                             \
   } while (0)
 
-template <typename T>
-void dfree(T*& p) {
-  if (p) cudaFree((void*)p);
-  p = nullptr;
-}
-
 }  // namespace
 
 int fora::report_error(int code, const char* fmt, ...) {
@@ -56,105 +51,46 @@ int fora::report_error(int code, const char* fmt, ...) {
   return code;
 }
 
-struct fora_graph {
-  int64_t n = 0, m = 0, max_deg = 0;
-  uint64_t hub_chunks = 0;  // sum over nodes with d > kHubChunk of ceil(d / kHubChunk)
-  uint32_t* row = nullptr;
-  int32_t* col = nullptr;
-  uint32_t* indeg = nullptr;  // in-degrees (features of the learned r_max)
-  int device = 0;
-  int num_sms = 0;
-  Tuning tune;
-  std::mutex mu;
-
-  // workspace for up to `cap` sources
-  int cap = 0;
-  double* r = nullptr;
-  double* res = nullptr;
-  Tally* tally = nullptr;
-  unsigned long long* q[2] = {nullptr, nullptr};
-  unsigned long long* hub[2] = {nullptr, nullptr};
-  double* fa = nullptr;
-  unsigned long long* small = nullptr;  // counters[4] totals[2]
-  uint32_t* mask = nullptr;
-  uint32_t* hubw = nullptr;
-  unsigned long long* work = nullptr;
-  uint32_t* active = nullptr;
-  uint32_t* err = nullptr;
-  int32_t* sources = nullptr;
-  double* rmax = nullptr;
-  SlotStats* stats = nullptr;
-  unsigned long long* blk = nullptr;  // [2][residual_grid]
-  int residual_grid = 0;
-  void* topk_scratch = nullptr;
-  float* feat = nullptr;        // learned r_max: features [cap][16], predictions, r_max
-  float* pred = nullptr;
-  double* rmax_learned = nullptr;
-  int32_t* out_ids = nullptr;  // device staging of host-bound results [cap][FORA_MAX_K]
-  double* out_vals = nullptr;
-  // pinned host mirrors
-  unsigned long long* h_counters = nullptr;
-  SlotStats* h_stats = nullptr;
-  uint32_t* h_err = nullptr;
-  int32_t* h_sources = nullptr;
-  double* h_rmax = nullptr;
-  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-
-  void release_workspace() {
-    dfree(r); dfree(res); dfree(tally);
-    dfree(q[0]); dfree(q[1]); dfree(hub[0]); dfree(hub[1]); dfree(fa);
-    dfree(small); dfree(mask); dfree(hubw); dfree(work); dfree(active); dfree(err); dfree(sources); dfree(rmax); dfree(stats); dfree(blk);
-    if (topk_scratch) cudaFree(topk_scratch);
-    topk_scratch = nullptr;
-    dfree(out_ids); dfree(out_vals); dfree(feat); dfree(pred); dfree(rmax_learned);
-    if (h_counters) cudaFreeHost(h_counters);
-    if (h_stats) cudaFreeHost(h_stats);
-    if (h_err) cudaFreeHost(h_err);
-    if (h_sources) cudaFreeHost(h_sources);
-    if (h_rmax) cudaFreeHost(h_rmax);
-    h_counters = nullptr; h_stats = nullptr; h_err = nullptr; h_sources = nullptr; h_rmax = nullptr;
-    cap = 0;
-  }
-};
-
 namespace {
 
-int ensure_workspace(fora_graph* g, int nsrc) {
-  if (nsrc <= g->cap) return FORA_OK;
-  g->release_workspace();
+int ensure_workspace(fora_graph* g, Workspace* w, int nsrc) {
+  if (nsrc <= w->cap) return FORA_OK;
+  w->release();
   const size_t N = (size_t)nsrc * (size_t)g->n;
   const size_t H = (size_t)nsrc * g->hub_chunks + 1;
-  g->residual_grid = g->num_sms * 8;
-  CUDA_TRY(cudaMalloc(&g->r, N * sizeof(double)));
-  CUDA_TRY(cudaMalloc(&g->res, N * sizeof(double)));
-  CUDA_TRY(cudaMalloc(&g->tally, N * sizeof(Tally)));
-  CUDA_TRY(cudaMalloc(&g->q[0], (N + 1) * sizeof(unsigned long long)));
-  CUDA_TRY(cudaMalloc(&g->q[1], (N + 1) * sizeof(unsigned long long)));
-  CUDA_TRY(cudaMalloc(&g->fa, (N + 1) * sizeof(double)));
-  CUDA_TRY(cudaMalloc(&g->hub[0], H * sizeof(unsigned long long)));
-  CUDA_TRY(cudaMalloc(&g->hub[1], H * sizeof(unsigned long long)));
-  CUDA_TRY(cudaMalloc(&g->small, 8 * sizeof(unsigned long long)));
-  CUDA_TRY(cudaMalloc(&g->mask, (size_t)nsrc * (((size_t)g->n + 31) / 32) * sizeof(uint32_t)));
-  CUDA_TRY(cudaMalloc(&g->hubw, (size_t)nsrc * (((size_t)g->n + 31) / 32) * sizeof(uint32_t)));
-  CUDA_TRY(cudaMalloc(&g->work, 32 * sizeof(unsigned long long)));
-  CUDA_TRY(cudaMalloc(&g->active, 2 * (size_t)nsrc * sizeof(uint32_t)));
-  CUDA_TRY(cudaMalloc(&g->err, sizeof(uint32_t)));
-  CUDA_TRY(cudaMalloc(&g->sources, nsrc * sizeof(int32_t)));
-  CUDA_TRY(cudaMalloc(&g->rmax, nsrc * sizeof(double)));
-  CUDA_TRY(cudaMalloc(&g->stats, nsrc * sizeof(SlotStats)));
-  CUDA_TRY(cudaMalloc(&g->blk, 2 * (size_t)g->residual_grid * sizeof(unsigned long long)));
-  CUDA_TRY(cudaMalloc(&g->topk_scratch, topk_scratch_bytes(nsrc)));
-  CUDA_TRY(cudaMalloc(&g->feat, (size_t)nsrc * FORA_NUM_FEATURES * sizeof(float)));
-  CUDA_TRY(cudaMalloc(&g->pred, (size_t)nsrc * sizeof(float)));
-  CUDA_TRY(cudaMalloc(&g->rmax_learned, (size_t)nsrc * sizeof(double)));
-  CUDA_TRY(cudaMalloc(&g->out_ids, (size_t)nsrc * FORA_MAX_K * sizeof(int32_t)));
-  CUDA_TRY(cudaMalloc(&g->out_vals, (size_t)nsrc * FORA_MAX_K * sizeof(double)));
-  CUDA_TRY(cudaMallocHost(&g->h_counters, 8 * sizeof(unsigned long long)));
-  CUDA_TRY(cudaMallocHost(&g->h_stats, nsrc * sizeof(SlotStats)));
-  CUDA_TRY(cudaMallocHost(&g->h_err, sizeof(uint32_t)));
-  CUDA_TRY(cudaMallocHost(&g->h_sources, nsrc * sizeof(int32_t)));
-  CUDA_TRY(cudaMallocHost(&g->h_rmax, nsrc * sizeof(double)));
-  g->cap = nsrc;
+  w->residual_grid = g->num_sms * 8;
+  CUDA_TRY(cudaMalloc(&w->r, N * sizeof(double)));
+  CUDA_TRY(cudaMalloc(&w->res, N * sizeof(double)));
+  CUDA_TRY(cudaMalloc(&w->tally, N * sizeof(Tally)));
+  CUDA_TRY(cudaMalloc(&w->q[0], (N + 1) * sizeof(unsigned long long)));
+  CUDA_TRY(cudaMalloc(&w->q[1], (N + 1) * sizeof(unsigned long long)));
+  CUDA_TRY(cudaMalloc(&w->fa, (N + 1) * sizeof(double)));
+  CUDA_TRY(cudaMalloc(&w->hub[0], H * sizeof(unsigned long long)));
+  CUDA_TRY(cudaMalloc(&w->hub[1], H * sizeof(unsigned long long)));
+  CUDA_TRY(cudaMalloc(&w->small, 8 * sizeof(unsigned long long)));
+  CUDA_TRY(cudaMalloc(&w->mask, (size_t)nsrc * (((size_t)g->n + 31) / 32) * sizeof(uint32_t)));
+  CUDA_TRY(cudaMalloc(&w->hubw, (size_t)nsrc * (((size_t)g->n + 31) / 32) * sizeof(uint32_t)));
+  CUDA_TRY(cudaMalloc(&w->work, 32 * sizeof(unsigned long long)));
+  CUDA_TRY(cudaMalloc(&w->active, 2 * (size_t)nsrc * sizeof(uint32_t)));
+  CUDA_TRY(cudaMalloc(&w->err, sizeof(uint32_t)));
+  CUDA_TRY(cudaMalloc(&w->sources, nsrc * sizeof(int32_t)));
+  CUDA_TRY(cudaMalloc(&w->rmax, nsrc * sizeof(double)));
+  CUDA_TRY(cudaMalloc(&w->stats, nsrc * sizeof(SlotStats)));
+  CUDA_TRY(cudaMalloc(&w->blk, 2 * (size_t)w->residual_grid * sizeof(unsigned long long)));
+  CUDA_TRY(cudaMalloc(&w->topk_scratch, topk_scratch_bytes(nsrc)));
+  CUDA_TRY(cudaMalloc(&w->feat, (size_t)nsrc * FORA_NUM_FEATURES * sizeof(float)));
+  CUDA_TRY(cudaMalloc(&w->pred, (size_t)nsrc * sizeof(float)));
+  CUDA_TRY(cudaMalloc(&w->rmax_learned, (size_t)nsrc * sizeof(double)));
+  CUDA_TRY(cudaMalloc(&w->out_ids, (size_t)nsrc * FORA_MAX_K * sizeof(int32_t)));
+  CUDA_TRY(cudaMalloc(&w->out_vals, (size_t)nsrc * FORA_MAX_K * sizeof(double)));
+  CUDA_TRY(cudaMallocHost(&w->h_counters, 8 * sizeof(unsigned long long)));
+  CUDA_TRY(cudaMallocHost(&w->h_stats, nsrc * sizeof(SlotStats)));
+  CUDA_TRY(cudaMallocHost(&w->h_err, sizeof(uint32_t)));
+  CUDA_TRY(cudaMallocHost(&w->h_sources, nsrc * sizeof(int32_t)));
+  CUDA_TRY(cudaMallocHost(&w->h_rmax, nsrc * sizeof(double)));
+  for (int i = 0; i < 5; ++i)
+    if (!w->ev[i]) CUDA_TRY(cudaEventCreate(&w->ev[i]));
+  w->cap = nsrc;
   return FORA_OK;
 }
 
@@ -192,15 +128,19 @@ int resolve(const fora_graph* g, const fora_params* p, Resolved* out) {
   return FORA_OK;
 }
 
-// Per-source residue thresholds: a host array, or a device array (learned r_max).
-struct RmaxSource {
-  const double* host = nullptr;
-  const double* device = nullptr;
-};
+}  // namespace
 
-int run_batch(fora_graph* g, const fora_params* p, const int32_t* sources, int nsrc,
-              int32_t* out_ids, double* out_vals, fora_stats* st, const fora_debug_io* dbg,
-              uint32_t dbg_flags, cudaStream_t stream, RmaxSource rsrc = RmaxSource()) {
+int fora::reserve_workspace(fora_graph* g, Workspace* w, int nsrc) {
+  std::lock_guard<std::mutex> lock(w->mu);
+  CUDA_TRY(cudaSetDevice(g->device));
+  return ensure_workspace(g, w, nsrc);
+}
+
+// One batched query on workspace w (the whole phase sequence of include/fora.h).
+int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
+                       const int32_t* sources, int nsrc, int32_t* out_ids, double* out_vals,
+                       fora_stats* st, const fora_debug_io* dbg, uint32_t dbg_flags,
+                       cudaStream_t stream, RmaxSource rsrc) {
   Resolved rp;
   int rc = resolve(g, p, &rp);
   if (rc) return rc;
@@ -217,26 +157,26 @@ int run_batch(fora_graph* g, const fora_params* p, const int32_t* sources, int n
   for (int i = 0; i < nsrc; ++i)
     if (sources[i] < 0 || sources[i] >= g->n) return fail(FORA_ERR_BAD_ARG, "source %d out of range", i);
 
-  std::lock_guard<std::mutex> lock(g->mu);
+  std::lock_guard<std::mutex> lock(w->mu);
   CUDA_TRY(cudaSetDevice(g->device));
-  rc = ensure_workspace(g, nsrc);
+  rc = ensure_workspace(g, w, nsrc);
   if (rc) return rc;
   const size_t N = (size_t)nsrc * (size_t)g->n;
   for (int i = 0; i < nsrc; ++i) {
-    g->h_sources[i] = sources[i];
-    g->h_rmax[i] = rsrc.host ? rsrc.host[i] : rp.rmax;
-    if (!(g->h_rmax[i] > 0.0) || !std::isfinite(g->h_rmax[i]))
+    w->h_sources[i] = sources[i];
+    w->h_rmax[i] = rsrc.host ? rsrc.host[i] : rp.rmax;
+    if (!(w->h_rmax[i] > 0.0) || !std::isfinite(w->h_rmax[i]))
       return fail(FORA_ERR_BAD_ARG, "r_max of source %d must be positive and finite", i);
   }
-  CUDA_TRY(cudaMemcpyAsync(g->sources, g->h_sources, nsrc * sizeof(int32_t), cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(cudaMemcpyAsync(w->sources, w->h_sources, nsrc * sizeof(int32_t), cudaMemcpyHostToDevice, stream));
   if (rsrc.device)
-    CUDA_TRY(cudaMemcpyAsync(g->rmax, rsrc.device, nsrc * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    CUDA_TRY(cudaMemcpyAsync(w->rmax, rsrc.device, nsrc * sizeof(double), cudaMemcpyDeviceToDevice, stream));
   else
-    CUDA_TRY(cudaMemcpyAsync(g->rmax, g->h_rmax, nsrc * sizeof(double), cudaMemcpyHostToDevice, stream));
-  CUDA_TRY(cudaMemsetAsync(g->tally, 0, N * sizeof(Tally), stream));
-  CUDA_TRY(cudaMemsetAsync(g->small, 0, 8 * sizeof(unsigned long long), stream));
-  CUDA_TRY(cudaMemsetAsync(g->err, 0, sizeof(uint32_t), stream));
-  CUDA_TRY(cudaMemsetAsync(g->stats, 0, nsrc * sizeof(SlotStats), stream));
+    CUDA_TRY(cudaMemcpyAsync(w->rmax, w->h_rmax, nsrc * sizeof(double), cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(cudaMemsetAsync(w->tally, 0, N * sizeof(Tally), stream));
+  CUDA_TRY(cudaMemsetAsync(w->small, 0, 8 * sizeof(unsigned long long), stream));
+  CUDA_TRY(cudaMemsetAsync(w->err, 0, sizeof(uint32_t), stream));
+  CUDA_TRY(cudaMemsetAsync(w->stats, 0, nsrc * sizeof(SlotStats), stream));
 
   GraphDev gd{g->n, g->m, g->row, g->col};
   BatchDev b{};
@@ -246,94 +186,97 @@ int run_batch(fora_graph* g, const fora_params* p, const int32_t* sources, int n
   b.alpha_threshold = rp.alpha_threshold;
   b.seed = p->seed;
   b.zero_hop = (p->flags & FORA_ZERO_HOP) != 0;
-  b.r = g->r; b.res = g->res; b.tally = g->tally;
-  b.q[0] = g->q[0]; b.q[1] = g->q[1]; b.fa = g->fa;
-  b.hub[0] = g->hub[0]; b.hub[1] = g->hub[1];
-  b.counters = g->small;
-  b.mask = g->mask;
-  b.hubw = g->hubw;
-  b.work = g->work;
-  b.active = g->active;
-  b.totals = g->small + 4;
-  b.sources = g->sources; b.rmax = g->rmax; b.stats = g->stats; b.err = g->err;
-  b.wr_entry = g->q[0];
-  b.wr_offset = g->q[1];
-  b.wr_weight = reinterpret_cast<unsigned long long*>(g->fa);
-  b.blk_cnt = g->blk;
-  b.blk_walks = g->blk + g->residual_grid;
-  b.residual_grid = g->residual_grid;
-  b.spread_width = g->tune.spread_width;
+  b.r = w->r; b.res = w->res; b.tally = w->tally;
+  b.q[0] = w->q[0]; b.q[1] = w->q[1]; b.fa = w->fa;
+  b.hub[0] = w->hub[0]; b.hub[1] = w->hub[1];
+  b.counters = w->small;
+  b.mask = w->mask;
+  b.hubw = w->hubw;
+  b.work = w->work;
+  b.active = w->active;
+  b.totals = w->small + 4;
+  b.sources = w->sources; b.rmax = w->rmax; b.stats = w->stats; b.err = w->err;
+  b.wr_entry = w->q[0];
+  b.wr_offset = w->q[1];
+  b.wr_weight = reinterpret_cast<unsigned long long*>(w->fa);
+  b.blk_cnt = w->blk;
+  b.blk_walks = w->blk + w->residual_grid;
+  b.residual_grid = w->residual_grid;
+  {
+    std::lock_guard<std::mutex> tlock(g->mu);
+    b.spread_width = g->tune.spread_width;
+  }
 
   const bool timed = st != nullptr;
-  if (timed) CUDA_TRY(cudaEventRecord(g->ev[0], stream));
+  if (timed) CUDA_TRY(cudaEventRecord(w->ev[0], stream));
 
   // ---- push (Alg. 1) ----
   if (given) {
-    CUDA_TRY(cudaMemcpyAsync(g->res, dbg->reserve, N * sizeof(double), cudaMemcpyDeviceToDevice, stream));
-    CUDA_TRY(cudaMemcpyAsync(g->r, dbg->residue, N * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    CUDA_TRY(cudaMemcpyAsync(w->res, dbg->reserve, N * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    CUDA_TRY(cudaMemcpyAsync(w->r, dbg->residue, N * sizeof(double), cudaMemcpyDeviceToDevice, stream));
   } else {
-    CUDA_TRY(cudaMemsetAsync(g->r, 0, N * sizeof(double), stream));
-    CUDA_TRY(cudaMemsetAsync(g->res, 0, N * sizeof(double), stream));
+    CUDA_TRY(cudaMemsetAsync(w->r, 0, N * sizeof(double), stream));
+    CUDA_TRY(cudaMemsetAsync(w->res, 0, N * sizeof(double), stream));
     CUDA_TRY(launch_push_init(gd, b, stream));
-    CUDA_TRY(cudaMemcpyAsync(g->h_counters, g->small, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaMemcpyAsync(w->h_counters, w->small, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream));
     CUDA_TRY(cudaStreamSynchronize(stream));
     int cur = 0;
     uint32_t round = 0;
-    while (g->h_counters[cur * 2] > 0) {
+    while (w->h_counters[cur * 2] > 0) {
       if (++round > FORA_MAX_PUSH_ROUNDS)
         return fail(FORA_ERR_PUSH_NOT_CONVERGED, "push did not converge in %d rounds", FORA_MAX_PUSH_ROUNDS);
-      CUDA_TRY(launch_push_round(gd, b, cur, g->h_counters[cur * 2], g->h_counters[cur * 2 + 1], round,
+      CUDA_TRY(launch_push_round(gd, b, cur, w->h_counters[cur * 2], w->h_counters[cur * 2 + 1], round,
                                  g->num_sms, stream));
       const int nxt = cur ^ 1;
-      CUDA_TRY(cudaMemcpyAsync(g->h_counters + nxt * 2, g->small + nxt * 2, 2 * sizeof(unsigned long long),
+      CUDA_TRY(cudaMemcpyAsync(w->h_counters + nxt * 2, w->small + nxt * 2, 2 * sizeof(unsigned long long),
                                cudaMemcpyDeviceToHost, stream));
       CUDA_TRY(cudaStreamSynchronize(stream));
       cur = nxt;
     }
     if (dbg && dbg->reserve)
-      CUDA_TRY(cudaMemcpyAsync(dbg->reserve, g->res, N * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+      CUDA_TRY(cudaMemcpyAsync(dbg->reserve, w->res, N * sizeof(double), cudaMemcpyDeviceToDevice, stream));
     if (dbg && dbg->residue)
-      CUDA_TRY(cudaMemcpyAsync(dbg->residue, g->r, N * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+      CUDA_TRY(cudaMemcpyAsync(dbg->residue, w->r, N * sizeof(double), cudaMemcpyDeviceToDevice, stream));
   }
-  if (timed) CUDA_TRY(cudaEventRecord(g->ev[1], stream));
+  if (timed) CUDA_TRY(cudaEventRecord(w->ev[1], stream));
 
   // ---- walks (Alg. 2, lines 3-10) ----
   CUDA_TRY(launch_residuals(gd, b, stream));
-  if (timed) CUDA_TRY(cudaEventRecord(g->ev[2], stream));
+  if (timed) CUDA_TRY(cudaEventRecord(w->ev[2], stream));
   CUDA_TRY(launch_walks(gd, b, g->num_sms, stream));
-  if (timed) CUDA_TRY(cudaEventRecord(g->ev[3], stream));
+  if (timed) CUDA_TRY(cudaEventRecord(w->ev[3], stream));
   if (dbg && (dbg->count || dbg->acc))
-    CUDA_TRY(launch_unpack_tally(g->tally, dbg->count, reinterpret_cast<unsigned long long*>(dbg->acc), N,
+    CUDA_TRY(launch_unpack_tally(w->tally, dbg->count, reinterpret_cast<unsigned long long*>(dbg->acc), N,
                                  g->num_sms, stream));
 
   // ---- estimate and top-k (the residue array becomes the estimate) ----
-  CUDA_TRY(launch_estimate(g->res, g->tally, g->r, g->r, rp.alpha, b.zero_hop, N, g->num_sms, stream));
+  CUDA_TRY(launch_estimate(w->res, w->tally, w->r, w->r, rp.alpha, b.zero_hop, N, g->num_sms, stream));
   if (dbg && dbg->estimate)
-    CUDA_TRY(cudaMemcpyAsync(dbg->estimate, g->r, N * sizeof(double), cudaMemcpyDeviceToDevice, stream));
-  int32_t* ids_dev = out_dev ? out_ids : g->out_ids;
-  double* vals_dev = out_dev ? out_vals : g->out_vals;
-  CUDA_TRY(launch_topk(g->r, g->n, nsrc, p->k, ids_dev, vals_dev,
-                       topk_scratch_carve(g->topk_scratch, nsrc), g->num_sms, stream));
-  if (timed) CUDA_TRY(cudaEventRecord(g->ev[4], stream));
+    CUDA_TRY(cudaMemcpyAsync(dbg->estimate, w->r, N * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  int32_t* ids_dev = out_dev ? out_ids : w->out_ids;
+  double* vals_dev = out_dev ? out_vals : w->out_vals;
+  CUDA_TRY(launch_topk(w->r, g->n, nsrc, p->k, ids_dev, vals_dev,
+                       topk_scratch_carve(w->topk_scratch, nsrc), g->num_sms, stream));
+  if (timed) CUDA_TRY(cudaEventRecord(w->ev[4], stream));
   if (!out_dev && p->k > 0) {
-    CUDA_TRY(cudaMemcpyAsync(out_ids, g->out_ids, (size_t)nsrc * p->k * sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
-    CUDA_TRY(cudaMemcpyAsync(out_vals, g->out_vals, (size_t)nsrc * p->k * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaMemcpyAsync(out_ids, w->out_ids, (size_t)nsrc * p->k * sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaMemcpyAsync(out_vals, w->out_vals, (size_t)nsrc * p->k * sizeof(double), cudaMemcpyDeviceToHost, stream));
   }
   if (async) return FORA_OK;
-  CUDA_TRY(cudaMemcpyAsync(g->h_err, g->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
-  if (st) CUDA_TRY(cudaMemcpyAsync(g->h_stats, g->stats, nsrc * sizeof(SlotStats), cudaMemcpyDeviceToHost, stream));
+  CUDA_TRY(cudaMemcpyAsync(w->h_err, w->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
+  if (st) CUDA_TRY(cudaMemcpyAsync(w->h_stats, w->stats, nsrc * sizeof(SlotStats), cudaMemcpyDeviceToHost, stream));
   if (st && rsrc.device)
-    CUDA_TRY(cudaMemcpyAsync(g->h_rmax, g->rmax, nsrc * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaMemcpyAsync(w->h_rmax, w->rmax, nsrc * sizeof(double), cudaMemcpyDeviceToHost, stream));
   CUDA_TRY(cudaStreamSynchronize(stream));
-  if (*g->h_err & kErrWalkOverflow) return fail(FORA_ERR_WALK_OVERFLOW, "a source needs 2^32 or more walks");
-  if (*g->h_err & kErrWalkCap) return fail(FORA_ERR_WALK_CAP, "a walk exceeded %d moves", FORA_MAX_WALK_STEPS);
+  if (*w->h_err & kErrWalkOverflow) return fail(FORA_ERR_WALK_OVERFLOW, "a source needs 2^32 or more walks");
+  if (*w->h_err & kErrWalkCap) return fail(FORA_ERR_WALK_CAP, "a walk exceeded %d moves", FORA_MAX_WALK_STEPS);
   if (st) {
     float ms[4] = {0, 0, 0, 0};
-    for (int i = 0; i < 4; ++i) CUDA_TRY(cudaEventElapsedTime(&ms[i], g->ev[i], g->ev[i + 1]));
+    for (int i = 0; i < 4; ++i) CUDA_TRY(cudaEventElapsedTime(&ms[i], w->ev[i], w->ev[i + 1]));
     for (int i = 0; i < nsrc; ++i) {
-      const SlotStats& s = g->h_stats[i];
+      const SlotStats& s = w->h_stats[i];
       fora_stats& o = st[i];
-      o.rmax = g->h_rmax[i];
+      o.rmax = w->h_rmax[i];
       o.rsum = s.rsum;
       o.pushes = s.pushes;
       o.edge_pushes = s.edge_pushes;
@@ -349,6 +292,15 @@ int run_batch(fora_graph* g, const fora_params* p, const int32_t* sources, int n
     }
   }
   return FORA_OK;
+}
+
+namespace {
+
+int run_batch(fora_graph* g, const fora_params* p, const int32_t* sources, int nsrc,
+              int32_t* out_ids, double* out_vals, fora_stats* st, const fora_debug_io* dbg,
+              uint32_t dbg_flags, cudaStream_t stream, RmaxSource rsrc = RmaxSource()) {
+  return run_batch_ws(g, &g->ws, p, sources, nsrc, out_ids, out_vals, st, dbg, dbg_flags, stream,
+                      rsrc);
 }
 
 }  // namespace
@@ -401,7 +353,6 @@ int fora_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col, uin
     e = launch_indegree(gd, g->indeg, g->num_sms, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
   }
-  for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = cudaEventCreate(&g->ev[i]);
   if (e != cudaSuccess)
     return bail(fail(e == cudaErrorMemoryAllocation ? FORA_ERR_OOM : FORA_ERR_CUDA, "graph upload: %s",
                      cudaGetErrorString(e)));
@@ -412,14 +363,12 @@ int fora_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col, uin
 void fora_graph_destroy(fora_graph* g) {
   if (!g) return;
   {
-    std::lock_guard<std::mutex> lock(g->mu);
+    std::lock_guard<std::mutex> lock(g->ws.mu);
     cudaSetDevice(g->device);
-    g->release_workspace();
+    g->ws.release();
     dfree(g->row);
     dfree(g->col);
     dfree(g->indeg);
-    for (int i = 0; i < 5; ++i)
-      if (g->ev[i]) cudaEventDestroy(g->ev[i]);
   }
   delete g;
 }
@@ -768,15 +717,20 @@ int fora_source_features(fora_graph* g, const fora_params* params, const int32_t
   if (!sources || nsrc < 1 || !out) return fail(FORA_ERR_BAD_ARG, "bad arguments");
   for (int i = 0; i < nsrc; ++i)
     if (sources[i] < 0 || sources[i] >= g->n) return fail(FORA_ERR_BAD_ARG, "source %d out of range", i);
-  std::lock_guard<std::mutex> lock(g->mu);
   CUDA_TRY(cudaSetDevice(g->device));
-  rc = ensure_workspace(g, nsrc);
-  if (rc) return rc;
-  memcpy(g->h_sources, sources, nsrc * sizeof(int32_t));
-  CUDA_TRY(cudaMemcpy(g->sources, g->h_sources, nsrc * sizeof(int32_t), cudaMemcpyHostToDevice));
+  // features need no query workspace: two small buffers of their own
+  int32_t* d_src = nullptr;
+  float* d_out = nullptr;
+  cudaError_t e = cudaMalloc(&d_src, (size_t)nsrc * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&d_out, (size_t)nsrc * FORA_NUM_FEATURES * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpy(d_src, sources, (size_t)nsrc * sizeof(int32_t), cudaMemcpyHostToDevice);
   GraphDev gd{g->n, g->m, g->row, g->col};
-  CUDA_TRY(launch_features(gd, g->indeg, g->sources, nsrc, rp.alpha, rp.rmax, g->feat, 0));
-  CUDA_TRY(cudaMemcpy(out, g->feat, (size_t)nsrc * FORA_NUM_FEATURES * sizeof(float), cudaMemcpyDeviceToHost));
+  if (e == cudaSuccess) e = launch_features(gd, g->indeg, d_src, nsrc, rp.alpha, rp.rmax, d_out, 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(out, d_out, (size_t)nsrc * FORA_NUM_FEATURES * sizeof(float), cudaMemcpyDeviceToHost);
+  dfree(d_src);
+  dfree(d_out);
+  CUDA_TRY(e);
   return FORA_OK;
 }
 
@@ -792,12 +746,13 @@ int fora_ssppr_batch_learned(fora_graph* g, const fora_params* params, fora_mode
     if (sources[i] < 0 || sources[i] >= g->n) return fail(FORA_ERR_BAD_ARG, "source %d out of range", i);
   cudaStream_t st = (cudaStream_t)stream;
   {
-    std::lock_guard<std::mutex> lock(g->mu);
+    Workspace* w = &g->ws;
+    std::lock_guard<std::mutex> lock(w->mu);
     CUDA_TRY(cudaSetDevice(g->device));
-    rc = ensure_workspace(g, nsrc);
+    rc = ensure_workspace(g, w, nsrc);
     if (rc) return rc;
-    memcpy(g->h_sources, sources, nsrc * sizeof(int32_t));
-    CUDA_TRY(cudaMemcpyAsync(g->sources, g->h_sources, nsrc * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    memcpy(w->h_sources, sources, nsrc * sizeof(int32_t));
+    CUDA_TRY(cudaMemcpyAsync(w->sources, w->h_sources, nsrc * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     GraphDev gd{g->n, g->m, g->row, g->col};
     // r_rule of these parameters (params->rmax is not used here)
     fora_params pr = *params;
@@ -805,13 +760,13 @@ int fora_ssppr_batch_learned(fora_graph* g, const fora_params* params, fora_mode
     Resolved rule;
     rc = resolve(g, &pr, &rule);
     if (rc) return rc;
-    CUDA_TRY(launch_features(gd, g->indeg, g->sources, nsrc, rule.alpha, rule.rmax, g->feat, st));
+    CUDA_TRY(launch_features(gd, g->indeg, w->sources, nsrc, rule.alpha, rule.rmax, w->feat, st));
     std::lock_guard<std::mutex> mlock(model->mu);
-    CUDA_TRY(launch_mlp_forward(model->master, model->norm, g->feat, nsrc, g->pred, st));
-    CUDA_TRY(launch_pred_to_rmax(g->pred, nsrc, rule.rmax, -3.0f, 3.0f, g->rmax_learned, st));
+    CUDA_TRY(launch_mlp_forward(model->master, model->norm, w->feat, nsrc, w->pred, st));
+    CUDA_TRY(launch_pred_to_rmax(w->pred, nsrc, rule.rmax, -3.0f, 3.0f, w->rmax_learned, st));
   }
   RmaxSource rs;
-  rs.device = g->rmax_learned;
+  rs.device = g->ws.rmax_learned;
   return run_batch(g, params, sources, nsrc, out_ids, out_vals, stats, nullptr, 0, st, rs);
 }
 

@@ -1,0 +1,110 @@
+// Host-side state of the query engine, shared by capi.cu and server.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "fora.h"
+#include "fora_engine.cuh"
+
+namespace fora {
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+// Device and pinned host buffers of one in-flight batched query (up to `cap` sources).
+// A graph owns one for its own entry points; the server owns one per lane.  A
+// workspace serves one call at a time (its mutex).
+struct Workspace {
+  // workspace for up to `cap` sources
+  int cap = 0;
+  double* r = nullptr;
+  double* res = nullptr;
+  Tally* tally = nullptr;
+  unsigned long long* q[2] = {nullptr, nullptr};
+  unsigned long long* hub[2] = {nullptr, nullptr};
+  double* fa = nullptr;
+  unsigned long long* small = nullptr;  // counters[4] totals[2]
+  uint32_t* mask = nullptr;
+  uint32_t* hubw = nullptr;
+  unsigned long long* work = nullptr;
+  uint32_t* active = nullptr;
+  uint32_t* err = nullptr;
+  int32_t* sources = nullptr;
+  double* rmax = nullptr;
+  SlotStats* stats = nullptr;
+  unsigned long long* blk = nullptr;  // [2][residual_grid]
+  int residual_grid = 0;
+  void* topk_scratch = nullptr;
+  float* feat = nullptr;        // learned r_max: features [cap][16], predictions, r_max
+  float* pred = nullptr;
+  double* rmax_learned = nullptr;
+  int32_t* out_ids = nullptr;  // device staging of host-bound results [cap][FORA_MAX_K]
+  double* out_vals = nullptr;
+  // pinned host mirrors
+  unsigned long long* h_counters = nullptr;
+  SlotStats* h_stats = nullptr;
+  uint32_t* h_err = nullptr;
+  int32_t* h_sources = nullptr;
+  double* h_rmax = nullptr;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+
+  std::mutex mu;
+
+  void release() {
+    dfree(r); dfree(res); dfree(tally);
+    dfree(q[0]); dfree(q[1]); dfree(hub[0]); dfree(hub[1]); dfree(fa);
+    dfree(small); dfree(mask); dfree(hubw); dfree(work); dfree(active); dfree(err); dfree(sources); dfree(rmax); dfree(stats); dfree(blk);
+    if (topk_scratch) cudaFree(topk_scratch);
+    topk_scratch = nullptr;
+    dfree(out_ids); dfree(out_vals); dfree(feat); dfree(pred); dfree(rmax_learned);
+    if (h_counters) cudaFreeHost(h_counters);
+    if (h_stats) cudaFreeHost(h_stats);
+    if (h_err) cudaFreeHost(h_err);
+    if (h_sources) cudaFreeHost(h_sources);
+    if (h_rmax) cudaFreeHost(h_rmax);
+    h_counters = nullptr; h_stats = nullptr; h_err = nullptr; h_sources = nullptr; h_rmax = nullptr;
+    cap = 0;
+  }
+  ~Workspace() {
+    release();
+    for (int i = 0; i < 5; ++i)
+      if (ev[i]) cudaEventDestroy(ev[i]);
+  }
+};
+
+}  // namespace fora
+
+struct fora_graph {
+  int64_t n = 0, m = 0, max_deg = 0;
+  uint64_t hub_chunks = 0;  // sum over nodes with d > kHubChunk of ceil(d / kHubChunk)
+  uint32_t* row = nullptr;
+  int32_t* col = nullptr;
+  uint32_t* indeg = nullptr;  // in-degrees (features of the learned r_max)
+  int device = 0;
+  int num_sms = 0;
+  fora::Tuning tune;
+  std::mutex mu;              // guards `tune`
+  fora::Workspace ws;         // the graph's own entry points
+};
+
+namespace fora {
+
+// Engine entry points (capi.cu).
+int report_error(int code, const char* fmt, ...);
+struct RmaxSource {
+  const double* host = nullptr;
+  const double* device = nullptr;
+};
+// Allocate w for nsrc queries of g now (under w's lock).
+int reserve_workspace(fora_graph* g, Workspace* w, int nsrc);
+int run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p, const int32_t* sources,
+                 int nsrc, int32_t* out_ids, double* out_vals, fora_stats* st,
+                 const fora_debug_io* dbg, uint32_t dbg_flags, cudaStream_t stream,
+                 RmaxSource rsrc);
+
+}  // namespace fora

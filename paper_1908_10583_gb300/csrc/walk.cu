@@ -31,6 +31,30 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
   return c;
 }
 
+// L2 eviction priorities (PTX createpolicy / ld.L2::cache_hint): the graph is read by
+// every walk and should outlive the streams of residual entries that pass through L2
+// once per chunk.
+__device__ __forceinline__ unsigned long long policy_evict_last() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ unsigned long long policy_evict_first() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint32_t ld_hint_u32(const void* ptr, unsigned long long pol) {
+  uint32_t v;
+  asm volatile("ld.global.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(ptr), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_hint_u64(const void* ptr, unsigned long long pol) {
+  unsigned long long v;
+  asm volatile("ld.global.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(ptr), "l"(pol));
+  return v;
+}
+
 // The word stream of one walk: blocks c = 0, 1, ... of Philox with counter (c, j, v, s).
 struct WalkStream {
   uint32_t c, j, v, s;
@@ -246,6 +270,8 @@ __global__ void __launch_bounds__(kWalkThreads) k_walks(GraphDev g, BatchDev b) 
   unsigned long long steps_here = 0;  // moves of this lane's walks of source `cur_slot`
   uint32_t cur_slot = 0xFFFFFFFFu;
   bool capped = false;
+  const unsigned long long keep = policy_evict_last();    // graph
+  const unsigned long long stream = policy_evict_first(); // residual entries
 
   for (unsigned long long c = warp; c < nchunks; c += nwarps) {
     const unsigned long long cbeg = c * kChunk;
@@ -277,12 +303,12 @@ __global__ void __launch_bounds__(kWalkThreads) k_walks(GraphDev g, BatchDev b) 
     bool forced = b.zero_hop;  // a pruned walk first moves without a stop test
     if (have) {
       const unsigned long long idx = idx0 + smap[wid][i];
-      const unsigned long long entry = b.wr_entry[idx];
+      const unsigned long long entry = ld_hint_u64(b.wr_entry + idx, stream);
       slot = (uint32_t)(entry >> 32);
       x = (uint32_t)entry;
-      rng.c = 0; rng.j = (uint32_t)(cbeg + i - off[idx]); rng.v = x;
+      rng.c = 0; rng.j = (uint32_t)(cbeg + i - ld_hint_u64(off + idx, stream)); rng.v = x;
       rng.s = (uint32_t)b.sources[slot]; rng.avail = 0;
-      wgt = b.wr_weight[idx];
+      wgt = ld_hint_u64(b.wr_weight + idx, stream);
       steps = 0;
     }
     while (have) {
@@ -301,12 +327,12 @@ __global__ void __launch_bounds__(kWalkThreads) k_walks(GraphDev g, BatchDev b) 
         have = i < cnt;
         if (have) {
           const unsigned long long idx = idx0 + smap[wid][i];
-          const unsigned long long entry = b.wr_entry[idx];
+          const unsigned long long entry = ld_hint_u64(b.wr_entry + idx, stream);
           slot = (uint32_t)(entry >> 32);
           x = (uint32_t)entry;
-          rng.c = 0; rng.j = (uint32_t)(cbeg + i - off[idx]); rng.v = x;
+          rng.c = 0; rng.j = (uint32_t)(cbeg + i - ld_hint_u64(off + idx, stream)); rng.v = x;
           rng.s = (uint32_t)b.sources[slot]; rng.avail = 0;
-          wgt = b.wr_weight[idx];
+          wgt = ld_hint_u64(b.wr_weight + idx, stream);
           steps = 0;
           forced = b.zero_hop;
         }
@@ -314,8 +340,8 @@ __global__ void __launch_bounds__(kWalkThreads) k_walks(GraphDev g, BatchDev b) 
       }
       forced = false;
       if (steps >= kMaxSteps) { capped = true; have = false; break; }
-      const uint32_t rb0 = g.row[x];
-      const uint32_t d = g.row[x + 1] - rb0;
+      const uint32_t rb0 = ld_hint_u32(g.row + x, keep);
+      const uint32_t d = ld_hint_u32(g.row + x + 1, keep) - rb0;
       unsigned long long m = (unsigned long long)rng.next() * d;
       uint32_t low = (uint32_t)m;
       if (low < d) {
@@ -327,7 +353,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walks(GraphDev g, BatchDev b) 
         }
         if (low < reject_below) { capped = true; have = false; break; }
       }
-      x = (uint32_t)g.col[rb0 + (uint32_t)(m >> 32)];
+      x = ld_hint_u32(g.col + rb0 + (uint32_t)(m >> 32), keep);
       ++steps;
     }
     __syncwarp();

@@ -159,7 +159,7 @@ def main(argv=None):
     cnt, runs, _ = measure(g, tr, params, batch=args.batch)
     coef = calibrate(runs)
     y = labels(cost(cnt, coef))
-    x = g.features(tr, params)
+    x = np.concatenate([g.features(tr[i:i + 4096], params) for i in range(0, len(tr), 4096)])
     t1 = time.time()
     model, hist = train(x, y, epochs=args.epochs, batch=256)
     t2 = time.time()

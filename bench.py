@@ -52,6 +52,8 @@ def parse_args():
     ap.add_argument("--rmax", choices=["auto", "rule", "learned"], default="auto",
                     help="learned: per-source r_max from paper_1908_10583_gb300/models/"
                          "rmax_<workload>.npz (auto: when that file exists)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip fora_graph_autotune (launch shapes at their defaults / --tune)")
     ap.add_argument("--plain-sources", type=int, default=16,
                     help="single-source queries timed for the plain-FORA comparison")
     return ap.parse_args()
@@ -259,6 +261,9 @@ def run_fora(args):
                 collect(step, st, out[-1])
         return out
 
+    if not args.no_autotune and not args.tune:
+        # autotuned frontier segments and walk-block shapes on a batch of the workload
+        tuning.update(g.autotune(sources(-100), params, stream=stream))
     for i in range(args.warmup):
         one_step(sources(-1 - i), model)
     torch.cuda.synchronize()

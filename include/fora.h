@@ -334,9 +334,22 @@ int fora_philox_debug(const uint32_t *ctr_key, uint32_t *out, int32_t count);
  * speed):  "spread_width" (1..4096, default 1): the push visits the sorted frontier of a
  * round through this many interleaved segments, so the warps in flight cover about that
  * many sources at once (wider spreads reductions on shared hub targets over more
- * addresses; narrower keeps the residue arrays in flight smaller).
+ * addresses; narrower keeps the residue arrays in flight smaller).  "walk_blocks" (4, 5
+ * or 6, default 4): resident walk blocks per SM, traded against registers per thread.
  */
 int fora_graph_tune(fora_graph *g, const char *key, int64_t value);
+
+/*
+ * Autotuner over the launch shapes of fora_graph_tune: runs the batched query on the
+ * given sources (HOST array, a representative batch) once to warm up, then with
+ * spread_width 1, 2, 4, 8, 16 keeping the fastest push phase, then with walk_blocks
+ * 4, 5, 6 ("walk_blocks": resident 256-thread walk blocks per SM, i.e. the register
+ * budget of the walk kernel) keeping the fastest walk phase.  The choices stay set on
+ * the graph and are returned (either pointer may be NULL).  Results of queries do not
+ * depend on them.
+ */
+int fora_graph_autotune(fora_graph *g, const fora_params *params, const int32_t *sources,
+                        int32_t nsrc, int32_t *spread_width, int32_t *walk_blocks, void *stream);
 
 /* Message of the calling thread's last failure ("" if none). */
 const char *fora_last_error(void);

@@ -155,6 +155,8 @@ def load():
         L.fora_server_wait.argtypes = [P, ctypes.c_uint64, ctypes.c_double, P, P, P]
         L.fora_server_stats.restype = I
         L.fora_server_stats.argtypes = [P, P, P, P]
+        L.fora_graph_autotune.restype = I
+        L.fora_graph_autotune.argtypes = [P, ctypes.POINTER(Params), P, i32, P, P, P]
         L.fora_graph_tune.restype = I
         L.fora_graph_tune.argtypes = [P, ctypes.c_char_p, i64]
         L.fora_last_error.restype = ctypes.c_char_p
@@ -223,6 +225,15 @@ class Graph:
     def tune(self, key: str, value: int):
         """Set a launch-shape parameter (fora_graph_tune); results do not depend on it."""
         _check(load().fora_graph_tune(self._h, key.encode(), int(value)))
+
+    def autotune(self, sources, params: Params, stream=None):
+        """fora_graph_autotune on a representative batch -> {spread_width, walk_blocks}."""
+        src = np.ascontiguousarray(sources, dtype=np.int32)
+        sw, wb = ctypes.c_int32(), ctypes.c_int32()
+        _check(load().fora_graph_autotune(self._h, ctypes.byref(params), src.ctypes.data,
+                                          len(src), ctypes.byref(sw), ctypes.byref(wb),
+                                          _stream_ptr(stream)))
+        return {"spread_width": sw.value, "walk_blocks": wb.value}
 
     def info(self):
         n, m, d = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()

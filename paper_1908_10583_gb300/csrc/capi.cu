@@ -72,6 +72,8 @@ int ensure_workspace(fora_graph* g, Workspace* w, int nsrc) {
   CUDA_TRY(cudaMalloc(&w->hubw, (size_t)nsrc * (((size_t)g->n + 31) / 32) * sizeof(uint32_t)));
   CUDA_TRY(cudaMalloc(&w->work, 32 * sizeof(unsigned long long)));
   CUDA_TRY(cudaMalloc(&w->active, 2 * (size_t)nsrc * sizeof(uint32_t)));
+  CUDA_TRY(cudaMalloc(&w->ps, sizeof(PushState)));
+  if (!w->capture_stream) CUDA_TRY(cudaStreamCreateWithFlags(&w->capture_stream, cudaStreamNonBlocking));
   CUDA_TRY(cudaMalloc(&w->err, sizeof(uint32_t)));
   CUDA_TRY(cudaMalloc(&w->sources, nsrc * sizeof(int32_t)));
   CUDA_TRY(cudaMalloc(&w->rmax, nsrc * sizeof(double)));
@@ -91,6 +93,7 @@ int ensure_workspace(fora_graph* g, Workspace* w, int nsrc) {
   for (int i = 0; i < 5; ++i)
     if (!w->ev[i]) CUDA_TRY(cudaEventCreate(&w->ev[i]));
   w->cap = nsrc;
+  ++w->generation;
   return FORA_OK;
 }
 
@@ -125,6 +128,53 @@ int resolve(const fora_graph* g, const fora_params* p, Resolved* out) {
     return fail(FORA_ERR_BAD_ARG, "parameters give a non-finite r_max or walk count");
   r.alpha_threshold = (uint32_t)floor(r.alpha * 4294967296.0);
   *out = r;
+  return FORA_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// The push rounds as a CUDA graph: one conditional while-node whose body is a round
+// (spread, detect, scan, emit, advance); the advance kernel sets the loop condition.
+// The instantiated graph is kept in the workspace and rebuilt when the workspace, the
+// number of sources, alpha or the launch shape change.
+int push_loop_graph(fora_graph* g, Workspace* w, const GraphDev& gd, const BatchDev& b) {
+  const PushGraphKey key{w->generation, b.nsrc, b.alpha, b.spread_width};
+  if (w->push_exec && key == w->push_key) return FORA_OK;
+  if (w->push_exec) {
+    cudaGraphExecDestroy(w->push_exec);
+    w->push_exec = nullptr;
+  }
+  cudaGraph_t graph = nullptr;
+  CUDA_TRY(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle loop;
+  cudaGraphNode_t node;
+  cudaGraphNodeParams np{};
+  cudaGraph_t captured = nullptr;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&loop, graph, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = loop;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+  }
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(w->capture_stream, np.conditional.phGraph_out[0], nullptr,
+                                      nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    const cudaError_t le = launch_push_body(gd, b, g->num_sms, loop, w->capture_stream);
+    e = cudaStreamEndCapture(w->capture_stream, &captured);
+    if (le != cudaSuccess) e = le;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&w->push_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    w->push_exec = nullptr;
+    return fail(FORA_ERR_CUDA, "push loop graph: %s", cudaGetErrorString(e));
+  }
+  w->push_key = key;
   return FORA_OK;
 }
 
@@ -194,6 +244,7 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
   b.hubw = w->hubw;
   b.work = w->work;
   b.active = w->active;
+  b.ps = w->ps;
   b.totals = w->small + 4;
   b.sources = w->sources; b.rmax = w->rmax; b.stats = w->stats; b.err = w->err;
   b.wr_entry = w->q[0];
@@ -205,6 +256,7 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
   {
     std::lock_guard<std::mutex> tlock(g->mu);
     b.spread_width = g->tune.spread_width;
+    b.walk_blocks = g->tune.walk_blocks;
   }
 
   const bool timed = st != nullptr;
@@ -217,22 +269,12 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
   } else {
     CUDA_TRY(cudaMemsetAsync(w->r, 0, N * sizeof(double), stream));
     CUDA_TRY(cudaMemsetAsync(w->res, 0, N * sizeof(double), stream));
-    CUDA_TRY(launch_push_init(gd, b, stream));
-    CUDA_TRY(cudaMemcpyAsync(w->h_counters, w->small, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream));
-    CUDA_TRY(cudaStreamSynchronize(stream));
-    int cur = 0;
-    uint32_t round = 0;
-    while (w->h_counters[cur * 2] > 0) {
-      if (++round > FORA_MAX_PUSH_ROUNDS)
-        return fail(FORA_ERR_PUSH_NOT_CONVERGED, "push did not converge in %d rounds", FORA_MAX_PUSH_ROUNDS);
-      CUDA_TRY(launch_push_round(gd, b, cur, w->h_counters[cur * 2], w->h_counters[cur * 2 + 1], round,
-                                 g->num_sms, stream));
-      const int nxt = cur ^ 1;
-      CUDA_TRY(cudaMemcpyAsync(w->h_counters + nxt * 2, w->small + nxt * 2, 2 * sizeof(unsigned long long),
-                               cudaMemcpyDeviceToHost, stream));
-      CUDA_TRY(cudaStreamSynchronize(stream));
-      cur = nxt;
-    }
+    CUDA_TRY(cudaMemsetAsync(w->work, 0, 32 * sizeof(unsigned long long), stream));
+    CUDA_TRY(launch_push_seed(gd, b, stream));
+    // the rounds run as a device-side while loop (no host round trip per round)
+    rc = push_loop_graph(g, w, gd, b);
+    if (rc) return rc;
+    CUDA_TRY(cudaGraphLaunch(w->push_exec, stream));
     if (dbg && dbg->reserve)
       CUDA_TRY(cudaMemcpyAsync(dbg->reserve, w->res, N * sizeof(double), cudaMemcpyDeviceToDevice, stream));
     if (dbg && dbg->residue)
@@ -268,6 +310,8 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
   if (st && rsrc.device)
     CUDA_TRY(cudaMemcpyAsync(w->h_rmax, w->rmax, nsrc * sizeof(double), cudaMemcpyDeviceToHost, stream));
   CUDA_TRY(cudaStreamSynchronize(stream));
+  if (*w->h_err & kErrPushNotConverged)
+    return fail(FORA_ERR_PUSH_NOT_CONVERGED, "push did not converge in %u rounds", kMaxPushRounds);
   if (*w->h_err & kErrWalkOverflow) return fail(FORA_ERR_WALK_OVERFLOW, "a source needs 2^32 or more walks");
   if (*w->h_err & kErrWalkCap) return fail(FORA_ERR_WALK_CAP, "a walk exceeded %d moves", FORA_MAX_WALK_STEPS);
   if (st) {
@@ -512,6 +556,11 @@ int fora_graph_tune(fora_graph* g, const char* key, int64_t value) {
   if (strcmp(key, "spread_width") == 0) {
     if (value < 1 || value > 4096) return fail(FORA_ERR_BAD_ARG, "spread_width must be in [1, 4096]");
     g->tune.spread_width = (int)value;
+    return FORA_OK;
+  }
+  if (strcmp(key, "walk_blocks") == 0) {
+    if (value < 4 || value > 6) return fail(FORA_ERR_BAD_ARG, "walk_blocks must be 4, 5 or 6");
+    g->tune.walk_blocks = (int)value;
     return FORA_OK;
   }
   return fail(FORA_ERR_BAD_ARG, "unknown tuning key '%s'", key);
@@ -768,6 +817,61 @@ int fora_ssppr_batch_learned(fora_graph* g, const fora_params* params, fora_mode
   RmaxSource rs;
   rs.device = g->ws.rmax_learned;
   return run_batch(g, params, sources, nsrc, out_ids, out_vals, stats, nullptr, 0, st, rs);
+}
+
+int fora_graph_autotune(fora_graph* g, const fora_params* params, const int32_t* sources,
+                        int32_t nsrc, int32_t* spread_width, int32_t* walk_blocks, void* stream) {
+  if (!g || !params || !sources || nsrc < 1) return fail(FORA_ERR_BAD_ARG, "bad arguments");
+  fora_params p = *params;
+  p.flags &= ~(FORA_OUT_DEVICE | FORA_ASYNC);
+  const uint32_t k = p.k;
+  std::vector<int32_t> ids((size_t)nsrc * (k ? k : 1));
+  std::vector<double> vals((size_t)nsrc * (k ? k : 1));
+  std::vector<fora_stats> st(nsrc);
+  auto run = [&](float* push_ms, float* walk_ms) {
+    const int rc = run_batch(g, &p, sources, nsrc, ids.data(), vals.data(), st.data(), nullptr, 0,
+                             (cudaStream_t)stream);
+    if (rc) return rc;
+    *push_ms = st[0].ms_push;
+    *walk_ms = st[0].ms_walk;
+    return FORA_OK;
+  };
+  float pm = 0, wm = 0;
+  int rc = run(&pm, &wm);  // warm-up: workspace and push-loop graph
+  if (rc) return rc;
+  // the push depends on spread_width only, the walk kernel on walk_blocks only
+  int best_sw = 1, best_wb = 4;
+  float best = 0;
+  const int widths[] = {1, 2, 4, 8, 16};
+  for (int i = 0; i < 5; ++i) {
+    {
+      std::lock_guard<std::mutex> lock(g->mu);
+      g->tune.spread_width = widths[i];
+    }
+    rc = run(&pm, &wm);
+    if (rc) return rc;
+    if (i == 0 || pm < best) { best = pm; best_sw = widths[i]; }
+  }
+  {
+    std::lock_guard<std::mutex> lock(g->mu);
+    g->tune.spread_width = best_sw;
+  }
+  for (int wb = 4; wb <= 6; ++wb) {
+    {
+      std::lock_guard<std::mutex> lock(g->mu);
+      g->tune.walk_blocks = wb;
+    }
+    rc = run(&pm, &wm);
+    if (rc) return rc;
+    if (wb == 4 || wm < best) { best = wm; best_wb = wb; }
+  }
+  {
+    std::lock_guard<std::mutex> lock(g->mu);
+    g->tune.walk_blocks = best_wb;
+  }
+  if (spread_width) *spread_width = best_sw;
+  if (walk_blocks) *walk_blocks = best_wb;
+  return FORA_OK;
 }
 
 const char* fora_last_error(void) { return g_err.c_str(); }

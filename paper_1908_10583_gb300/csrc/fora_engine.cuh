@@ -21,6 +21,15 @@ constexpr uint32_t kSortCap = 8192;  // candidates sorted in shared memory at th
 // Device error bits (ORed into BatchDev::err).
 constexpr uint32_t kErrWalkCap = 1u;
 constexpr uint32_t kErrWalkOverflow = 2u;
+constexpr uint32_t kErrPushNotConverged = 4u;
+constexpr uint32_t kMaxPushRounds = 100000u;
+
+// Where the push loop stands: the parity of the current frontier queue and the number
+// of rounds done.  Kept on the device so the loop runs without the host.
+struct PushState {
+  int cur;
+  uint32_t round;
+};
 
 struct GraphDev {
   int64_t n;
@@ -79,6 +88,7 @@ struct BatchDev {
   uint32_t* hubw;            // hub items of the crossing nodes of each mask word
   unsigned long long* work;  // dynamic work counters of the spread ([0] and [16])
   uint32_t* active;          // [2][nsrc]: sources with entries in q[0] / q[1]
+  PushState* ps;
   const int32_t* sources;    // [nsrc]
   const double* rmax;        // [nsrc]
   SlotStats* stats;          // [nsrc]
@@ -92,22 +102,23 @@ struct BatchDev {
   unsigned long long* totals;     // [2]: |R|, W
   int residual_grid;
   int spread_width;  // interleaved segments of the frontier the spread visits at once
+  int walk_blocks;   // resident walk blocks per SM (4, 5 or 6)
 };
 
-// Launch-shape parameters of a graph (set through fora_graph_tune).
+// Launch-shape parameters of a graph (set through fora_graph_tune or the autotuner).
 struct Tuning {
   int spread_width = 1;
+  int walk_blocks = 4;
 };
 
 // capi.cu: record a failure for fora_last_error() and return `code`.
 int report_error(int code, const char* fmt, ...);
 
-// push.cu
-cudaError_t launch_push_init(const GraphDev& g, const BatchDev& b, cudaStream_t st);
-cudaError_t launch_push_detect(const GraphDev& g, const BatchDev& b, int par, uint32_t round,
-                               cudaStream_t st);
-cudaError_t launch_push_round(const GraphDev& g, const BatchDev& b, int cur, uint64_t nf,
-                              uint64_t nh, uint32_t round, int num_sms, cudaStream_t st);
+// push.cu: r(s) = 1 and the loop state; then the rounds, each launched by the body of a
+// conditional while-node of a CUDA graph (the body sets the loop condition itself).
+cudaError_t launch_push_seed(const GraphDev& g, const BatchDev& b, cudaStream_t st);
+cudaError_t launch_push_body(const GraphDev& g, const BatchDev& b, int num_sms,
+                             cudaGraphConditionalHandle loop, cudaStream_t st);
 
 // walk.cu
 cudaError_t launch_residuals(const GraphDev& g, const BatchDev& b, cudaStream_t st);

@@ -79,9 +79,14 @@ __global__ void k_push_seed(GraphDev g, BatchDev b) {
   for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < b.nsrc;
        slot += gridDim.x * blockDim.x) {
     b.r[(unsigned long long)slot * (unsigned long long)g.n + (uint32_t)b.sources[slot]] = 1.0;
-    // Alg. 1, line 1: r(s) = 1.  The detection that builds F_0 runs with parity 1:
-    // it scans the sources flagged in active[1] and writes F_0 into q[0].
+    // Alg. 1, line 1: r(s) = 1.  The first pass of the loop body has an empty frontier
+    // of parity 1 (nothing to spread); its detection scans the sources flagged in
+    // active[1] and writes F_0 into q[0].
     b.active[b.nsrc + slot] = 1;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    b.ps->cur = 1;
+    b.ps->round = 0;
   }
 }
 
@@ -90,7 +95,8 @@ __global__ void k_push_seed(GraphDev g, BatchDev b) {
 // the cost of each group.
 constexpr unsigned long long kGrab = 4;
 
-__global__ void __launch_bounds__(kSpreadThreads) k_push_spread(GraphDev g, BatchDev b, int cur) {
+__global__ void __launch_bounds__(kSpreadThreads) k_push_spread(GraphDev g, BatchDev b) {
+  const int cur = b.ps->cur;
   const unsigned long long nf = b.counters[cur * 2];
   const unsigned long long nh = b.counters[cur * 2 + 1];
   const unsigned long long* q = b.q[cur];
@@ -205,7 +211,8 @@ __device__ __forceinline__ void word_range(unsigned long long total, int blk, in
 // padded to whole words) at a time; for word k the 32 lanes test 32 consecutive nodes
 // and the ballot of their tests is the mask word.  Eight words' residues are loaded
 // before any is used.
-__global__ void __launch_bounds__(kDetectThreads) k_push_detect(GraphDev g, BatchDev b, int par) {
+__global__ void __launch_bounds__(kDetectThreads) k_push_detect(GraphDev g, BatchDev b) {
+  const int par = b.ps->cur;
   const unsigned long long wps = words_per_slot(g.n);
   const unsigned long long total = (unsigned long long)b.nsrc * wps;
   unsigned long long wbeg, wend;
@@ -270,7 +277,8 @@ __global__ void __launch_bounds__(kDetectThreads) k_push_detect(GraphDev g, Batc
 }
 
 // One block: exclusive scan of the per-block counts; totals into the next counters.
-__global__ void __launch_bounds__(1024) k_push_scan(BatchDev b, int nxt) {
+__global__ void __launch_bounds__(1024) k_push_scan(BatchDev b) {
+  const int nxt = b.ps->cur ^ 1;
   __shared__ unsigned long long carry_n, carry_h;
   if (threadIdx.x == 0) { carry_n = 0; carry_h = 0; }
   __syncthreads();
@@ -299,8 +307,9 @@ __global__ void __launch_bounds__(1024) k_push_scan(BatchDev b, int nxt) {
 // Pass 2: write F_{t+1} in order and take the residue of its nodes.  The block walks its
 // word range in tiles of 32 words per warp; within a word the lanes are the 32 bits, so
 // the residue, reserve and degree reads and the frontier writes are coalesced.
-__global__ void __launch_bounds__(kDetectThreads) k_push_emit(GraphDev g, BatchDev b, int par,
-                                                              uint32_t round) {
+__global__ void __launch_bounds__(kDetectThreads) k_push_emit(GraphDev g, BatchDev b) {
+  const int par = b.ps->cur;
+  const uint32_t round = b.ps->round + 1;  // the take done here belongs to the next round
   const int nxt = par ^ 1;
   const unsigned long long wps = words_per_slot(g.n);
   const unsigned long long total = (unsigned long long)b.nsrc * wps;
@@ -401,33 +410,30 @@ __global__ void __launch_bounds__(kDetectThreads) k_push_emit(GraphDev g, BatchD
   }
 }
 
+// End of a round: switch to the new frontier and keep looping while it is non-empty
+// (at most kMaxPushRounds rounds).
+__global__ void k_push_advance(BatchDev b, cudaGraphConditionalHandle loop) {
+  PushState* ps = b.ps;
+  ps->cur ^= 1;
+  ps->round += 1;
+  const bool more = b.counters[ps->cur * 2] > 0;
+  const bool go = more && ps->round < kMaxPushRounds;
+  if (more && !go) atomicOr(b.err, kErrPushNotConverged);
+  cudaGraphSetConditional(loop, go ? 1u : 0u);
+}
+
 }  // namespace
 
-cudaError_t launch_push_detect(const GraphDev& g, const BatchDev& b, int par, uint32_t round,
-                               cudaStream_t st) {
-  k_push_detect<<<b.residual_grid, kDetectThreads, 0, st>>>(g, b, par);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_push_scan<<<1, 1024, 0, st>>>(b, par ^ 1);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_push_emit<<<b.residual_grid, kDetectThreads, 0, st>>>(g, b, par, round);
+cudaError_t launch_push_seed(const GraphDev& g, const BatchDev& b, cudaStream_t st) {
+  const int threads = 256;
+  k_push_seed<<<(b.nsrc + threads - 1) / threads, threads, 0, st>>>(g, b);
   return cudaGetLastError();
 }
 
-cudaError_t launch_push_init(const GraphDev& g, const BatchDev& b, cudaStream_t st) {
-  const int threads = 256;
-  k_push_seed<<<(b.nsrc + threads - 1) / threads, threads, 0, st>>>(g, b);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  // F_0 = {s} if 1 > r_max d(s): the detection pass over r = e_s, taken as round 1
-  return launch_push_detect(g, b, /*par=*/1, /*round=*/1, st);
-}
-
-cudaError_t launch_push_round(const GraphDev& g, const BatchDev& b, int cur, uint64_t nf,
-                              uint64_t nh, uint32_t round, int num_sms, cudaStream_t st) {
-  // At most one wave of resident blocks: with a grid-stride over the sorted frontier the
-  // warps in flight then cover one contiguous window of it (a few sources at a time).
+cudaError_t launch_push_body(const GraphDev& g, const BatchDev& b, int num_sms,
+                             cudaGraphConditionalHandle loop, cudaStream_t st) {
+  // one wave of resident blocks: with the dynamic work counter the warps in flight
+  // cover one contiguous window of the sorted frontier
   static int per_sm = 0;
   if (per_sm == 0) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push_spread,
@@ -435,17 +441,20 @@ cudaError_t launch_push_round(const GraphDev& g, const BatchDev& b, int cur, uin
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
   }
-  const uint64_t max_blocks = (uint64_t)num_sms * per_sm;
-  const uint64_t warps = (nf + 31) / 32 + nh;
-  uint64_t blocks = (warps * 32 + kSpreadThreads - 1) / kSpreadThreads;
-  if (blocks > max_blocks) blocks = max_blocks;
-  if (blocks == 0) blocks = 1;
-  k_push_spread<<<(unsigned)blocks, kSpreadThreads, 0, st>>>(g, b, cur);
+  k_push_spread<<<num_sms * per_sm, kSpreadThreads, 0, st>>>(g, b);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  // detection scans the sources that pushed in this round (flags of parity cur) and
-  // writes F_{round+1} into q[cur ^ 1], taking its residue as round round + 1
-  return launch_push_detect(g, b, cur, round + 1, st);
+  k_push_detect<<<b.residual_grid, kDetectThreads, 0, st>>>(g, b);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_push_scan<<<1, 1024, 0, st>>>(b);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_push_emit<<<b.residual_grid, kDetectThreads, 0, st>>>(g, b);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_push_advance<<<1, 1, 0, st>>>(b, loop);
+  return cudaGetLastError();
 }
 
 }  // namespace fora

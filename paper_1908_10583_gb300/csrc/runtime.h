@@ -16,6 +16,18 @@ void dfree(T*& p) {
   p = nullptr;
 }
 
+// What an instantiated push-loop graph was built for.
+struct PushGraphKey {
+  uint64_t generation = 0;
+  int nsrc = 0;
+  double alpha = 0.0;
+  int spread_width = 0;
+  bool operator==(const PushGraphKey& o) const {
+    return generation == o.generation && nsrc == o.nsrc && alpha == o.alpha &&
+           spread_width == o.spread_width;
+  }
+};
+
 // Device and pinned host buffers of one in-flight batched query (up to `cap` sources).
 // A graph owns one for its own entry points; the server owns one per lane.  A
 // workspace serves one call at a time (its mutex).
@@ -53,9 +65,17 @@ struct Workspace {
   double* h_rmax = nullptr;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 
+  PushState* ps = nullptr;
+  uint64_t generation = 0;               // bumped whenever the buffers are reallocated
+  cudaGraphExec_t push_exec = nullptr;   // the push rounds as a device-side loop
+  PushGraphKey push_key;
+  cudaStream_t capture_stream = nullptr; // for capturing the loop body
   std::mutex mu;
 
   void release() {
+    if (push_exec) cudaGraphExecDestroy(push_exec);
+    push_exec = nullptr;
+    dfree(ps);
     dfree(r); dfree(res); dfree(tally);
     dfree(q[0]); dfree(q[1]); dfree(hub[0]); dfree(hub[1]); dfree(fa);
     dfree(small); dfree(mask); dfree(hubw); dfree(work); dfree(active); dfree(err); dfree(sources); dfree(rmax); dfree(stats); dfree(blk);
@@ -72,6 +92,7 @@ struct Workspace {
   }
   ~Workspace() {
     release();
+    if (capture_stream) cudaStreamDestroy(capture_stream);
     for (int i = 0; i < 5; ++i)
       if (ev[i]) cudaEventDestroy(ev[i]);
   }

@@ -31,42 +31,35 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
   return c;
 }
 
-// L2 eviction priorities (PTX createpolicy / ld.L2::cache_hint): the graph is read by
-// every walk and should outlive the streams of residual entries that pass through L2
-// once per chunk.
-__device__ __forceinline__ unsigned long long policy_evict_last() {
-  unsigned long long p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ unsigned long long policy_evict_first() {
-  unsigned long long p;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ uint32_t ld_hint_u32(const void* ptr, unsigned long long pol) {
-  uint32_t v;
-  asm volatile("ld.global.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(ptr), "l"(pol));
-  return v;
-}
-__device__ __forceinline__ unsigned long long ld_hint_u64(const void* ptr, unsigned long long pol) {
-  unsigned long long v;
-  asm volatile("ld.global.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(ptr), "l"(pol));
-  return v;
-}
-
-// The word stream of one walk: blocks c = 0, 1, ... of Philox with counter (c, j, v, s).
+// The word stream of one walk: blocks c = 0, 1, ... of Philox with counter (c, j, v, s),
+// consumed in order.  Besides the current block a lane may hold the next one
+// (prefetched), so the walk loop can generate blocks for all lanes of a warp at the same
+// point instead of one lane at a time.
 struct WalkStream {
   uint32_t c, j, v, s;
   uint2 key;
-  uint32_t w0, w1, w2, w3;
-  int avail;
+  uint32_t w0, w1, w2, w3;  // current block, w0 is the next word
+  int avail;                // words left in the current block
+  uint32_t p0, p1, p2, p3;  // the next block, if pre
+  bool pre;
+  __device__ __forceinline__ void reset(uint32_t jj, uint32_t vv, uint32_t ss) {
+    c = 0; j = jj; v = vv; s = ss;
+    avail = 0;
+    pre = false;
+  }
+  __device__ __forceinline__ void prefetch() {
+    const uint4 o = philox4x32_10(make_uint4(c, j, v, s), key);
+    ++c;
+    p0 = o.x; p1 = o.y; p2 = o.z; p3 = o.w;
+    pre = true;
+  }
+  __device__ __forceinline__ int buffered() const { return avail + (pre ? 4 : 0); }
   __device__ __forceinline__ uint32_t next() {
     if (avail == 0) {
-      const uint4 o = philox4x32_10(make_uint4(c, j, v, s), key);
-      ++c;
-      w0 = o.x; w1 = o.y; w2 = o.z; w3 = o.w;
+      if (!pre) prefetch();
+      w0 = p0; w1 = p1; w2 = p2; w3 = p3;
       avail = 4;
+      pre = false;
     }
     const uint32_t r = w0;
     w0 = w1; w1 = w2; w2 = w3;
@@ -255,7 +248,8 @@ __device__ __forceinline__ unsigned long long warp_find_entry(const unsigned lon
 // Per chunk the warp first maps every walk to its residual entry (into shared
 // memory, relative to the chunk's first entry), then each lane runs its 32 walks
 // as an independent state machine (one move or one walk end per loop iteration).
-__global__ void __launch_bounds__(kWalkThreads) k_walks(GraphDev g, BatchDev b) {
+template <int kMinBlocks>
+__global__ void __launch_bounds__(kWalkThreads, kMinBlocks) k_walks(GraphDev g, BatchDev b) {
   __shared__ uint16_t smap[kWalkWarps][kChunk];
   if (*b.err) return;
   const unsigned long long W = b.totals[1];
@@ -270,8 +264,6 @@ __global__ void __launch_bounds__(kWalkThreads) k_walks(GraphDev g, BatchDev b) 
   unsigned long long steps_here = 0;  // moves of this lane's walks of source `cur_slot`
   uint32_t cur_slot = 0xFFFFFFFFu;
   bool capped = false;
-  const unsigned long long keep = policy_evict_last();    // graph
-  const unsigned long long stream = policy_evict_first(); // residual entries
 
   for (unsigned long long c = warp; c < nchunks; c += nwarps) {
     const unsigned long long cbeg = c * kChunk;
@@ -298,20 +290,25 @@ __global__ void __launch_bounds__(kWalkThreads) k_walks(GraphDev g, BatchDev b) 
     bool have = i < cnt;
     WalkStream rng;
     rng.key = key;
+    rng.pre = false;
+    rng.avail = 0;
     uint32_t x = 0, slot = 0, steps = 0;
     unsigned long long wgt = 0;
     bool forced = b.zero_hop;  // a pruned walk first moves without a stop test
     if (have) {
       const unsigned long long idx = idx0 + smap[wid][i];
-      const unsigned long long entry = ld_hint_u64(b.wr_entry + idx, stream);
+      const unsigned long long entry = b.wr_entry[idx];
       slot = (uint32_t)(entry >> 32);
       x = (uint32_t)entry;
-      rng.c = 0; rng.j = (uint32_t)(cbeg + i - ld_hint_u64(off + idx, stream)); rng.v = x;
-      rng.s = (uint32_t)b.sources[slot]; rng.avail = 0;
-      wgt = ld_hint_u64(b.wr_weight + idx, stream);
+      rng.reset((uint32_t)(cbeg + i - off[idx]), x, (uint32_t)b.sources[slot]);
+      wgt = b.wr_weight[idx];
       steps = 0;
     }
     while (have) {
+      // an iteration takes at most two words (stop test, neighbour draw) unless the draw
+      // is rejected; when any lane holds fewer, every lane without a prefetched block
+      // generates one, together
+      if (__any_sync(__activemask(), rng.buffered() < 2) && !rng.pre) rng.prefetch();
       if (!forced && rng.next() < t_alpha) {
         // the walk stops at x (Section 2.1): count it and add its weight (Alg. 2)
         Tally* t = b.tally + (unsigned long long)slot * (unsigned long long)g.n + x;
@@ -327,12 +324,11 @@ __global__ void __launch_bounds__(kWalkThreads) k_walks(GraphDev g, BatchDev b) 
         have = i < cnt;
         if (have) {
           const unsigned long long idx = idx0 + smap[wid][i];
-          const unsigned long long entry = ld_hint_u64(b.wr_entry + idx, stream);
+          const unsigned long long entry = b.wr_entry[idx];
           slot = (uint32_t)(entry >> 32);
           x = (uint32_t)entry;
-          rng.c = 0; rng.j = (uint32_t)(cbeg + i - ld_hint_u64(off + idx, stream)); rng.v = x;
-          rng.s = (uint32_t)b.sources[slot]; rng.avail = 0;
-          wgt = ld_hint_u64(b.wr_weight + idx, stream);
+          rng.reset((uint32_t)(cbeg + i - off[idx]), x, (uint32_t)b.sources[slot]);
+          wgt = b.wr_weight[idx];
           steps = 0;
           forced = b.zero_hop;
         }
@@ -340,8 +336,8 @@ __global__ void __launch_bounds__(kWalkThreads) k_walks(GraphDev g, BatchDev b) 
       }
       forced = false;
       if (steps >= kMaxSteps) { capped = true; have = false; break; }
-      const uint32_t rb0 = ld_hint_u32(g.row + x, keep);
-      const uint32_t d = ld_hint_u32(g.row + x + 1, keep) - rb0;
+      const uint32_t rb0 = g.row[x];
+      const uint32_t d = g.row[x + 1] - rb0;
       unsigned long long m = (unsigned long long)rng.next() * d;
       uint32_t low = (uint32_t)m;
       if (low < d) {
@@ -353,7 +349,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walks(GraphDev g, BatchDev b) 
         }
         if (low < reject_below) { capped = true; have = false; break; }
       }
-      x = ld_hint_u32(g.col + rb0 + (uint32_t)(m >> 32), keep);
+      x = (uint32_t)g.col[rb0 + (uint32_t)(m >> 32)];
       ++steps;
     }
     __syncwarp();
@@ -394,13 +390,27 @@ cudaError_t launch_residuals(const GraphDev& g, const BatchDev& b, cudaStream_t 
   return cudaGetLastError();
 }
 
-cudaError_t launch_walks(const GraphDev& g, const BatchDev& b, int num_sms, cudaStream_t st) {
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walks, kWalkThreads, 0);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
-  k_walks<<<num_sms * per_sm, kWalkThreads, 0, st>>>(g, b);
+// Walk kernel instances for 4, 5 or 6 resident blocks of 256 threads per SM (the
+// register budget the compiler gets); b.walk_blocks picks one (launch shape only).
+template <int kMinBlocks>
+cudaError_t launch_walks_t(const GraphDev& g, const BatchDev& b, int num_sms, cudaStream_t st) {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walks<kMinBlocks>,
+                                                                  kWalkThreads, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+  }
+  k_walks<kMinBlocks><<<num_sms * per_sm, kWalkThreads, 0, st>>>(g, b);
   return cudaGetLastError();
+}
+
+cudaError_t launch_walks(const GraphDev& g, const BatchDev& b, int num_sms, cudaStream_t st) {
+  switch (b.walk_blocks) {
+    case 6: return launch_walks_t<6>(g, b, num_sms, st);
+    case 5: return launch_walks_t<5>(g, b, num_sms, st);
+    default: return launch_walks_t<4>(g, b, num_sms, st);
+  }
 }
 
 cudaError_t launch_unpack_tally(const Tally* t, uint32_t* cnt, unsigned long long* acc,

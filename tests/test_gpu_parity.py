@@ -294,3 +294,29 @@ def test_topk_fora_matches_oracle(rmat14):
                 if true_sorted[j] > 1.0 / n:
                     assert vals[i][j] >= 0.5 * truth[i][v]
                     assert truth[i][v] >= 0.5 * true_sorted[j]
+
+
+def test_autotuner_and_launch_shapes_do_not_change_results(rmat14):
+    """fora_graph_autotune picks spread_width / walk_blocks by measured phase times; any
+    launch shape gives the same walk counts (same residues) and top-k up to the push
+    rounding."""
+    rp, col, g = rmat14
+    n = len(rp) - 1
+    sources = inputs.uniform_sources(n, 12, 4444)
+    p = fora.Params.make(k=50, seed=8)
+    ref_ids, ref_vals, ref_st, ref = run_debug(g, sources, p)
+    choice = g.autotune(sources, p)
+    assert choice["spread_width"] in (1, 2, 4, 8, 16) and choice["walk_blocks"] in (4, 5, 6)
+    for sw, wb in [(1, 4), (16, 5), (3, 6), (choice["spread_width"], choice["walk_blocks"])]:
+        g.tune("spread_width", sw)
+        g.tune("walk_blocks", wb)
+        ids, vals, st, out = run_debug(g, sources, p, given=(ref["reserve"], ref["residue"]))
+        np.testing.assert_array_equal(out["count"], ref["count"])
+        np.testing.assert_array_equal(ids, ref_ids)
+        _, vals2, st2, out2 = run_debug(g, sources, p)
+        np.testing.assert_allclose(out2["reserve"], ref["reserve"], rtol=0, atol=ATOL_PUSH)
+        assert [s.pushes for s in st2] == [s.pushes for s in ref_st]
+    with pytest.raises(fora.FORAError):
+        g.tune("walk_blocks", 7)
+    g.tune("spread_width", 1)
+    g.tune("walk_blocks", 4)

@@ -278,7 +278,9 @@ def run_fora(args):
 
     def collect(step, st, ms):
         rounds = max(s.push_rounds for s in st)
-        counters["launches"] += 4 + 4 * rounds + 3 + 1 + 1 + 19  # push, residuals, walks, top-k
+        # push: the seed, then (rounds + 1) passes of the graph loop body (spread, detect,
+        # scan, emit, advance); residuals 3, walks 1, estimate 1, top-k select 19
+        counters["launches"] += 1 + 5 * (rounds + 1) + 3 + 1 + 1 + 19
         if model is not None:
             counters["launches"] += 3  # features, forward, r_max
         for key in phase:

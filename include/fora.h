@@ -122,7 +122,7 @@ int fora_graph_info(const fora_graph *g, int64_t *n, int64_t *m, int64_t *max_de
 
 /*
  * Resolve the parameters as a query would: the r_max in use (rule of
- * Section 3.2 when params->rmax <= 0), C = omega / r_sum of Alg. 2 line 3,
+ * Section 3.2 when params->rmax <= 0), C = omega / r_sum of Alg. 2,
  * and the walk stop threshold floor(alpha * 2^32).  Any output may be NULL.
  */
 int fora_resolve_params(const fora_graph *g, const fora_params *params, double *rmax,

@@ -113,7 +113,7 @@ def _graph(row_ptr, col):
 
 
 def walk_scale(eps, delta, pf):
-    """C = omega / r_sum (Alg. 2, line 3)."""
+    """C = omega / r_sum (Alg. 2)."""
     return _load().oracle_walk_scale(eps, delta, pf)
 
 

@@ -10,7 +10,7 @@
  *
  * Steps and the passages they follow:
  *   - parameters: omega = r_sum * (2eps/3 + 2) * log(2/p_f) / (eps^2 delta)
- *     (Alg. 2, line 3) and the r_max rule (Eq. rmax, Section 3.2, with its
+ *     (Alg. 2) and the r_max rule (Eq. rmax, Section 3.2, with its
  *     Case 2 fallback when m * r_max > 1);
  *   - Forward Push (Alg. 1), run as synchronous rounds: round t takes the set
  *     F_t of every v with r(v)/d_out(v) > r_max (the reading "identifies every
@@ -18,7 +18,7 @@
  *     and zeroes r(v) for all of F_t, then spreads (1-alpha)*r(v)/d_out(v) to
  *     every out-neighbour; residue arriving at a node of F_t during round t
  *     waits for round t+1.  The test is written r(v) > r_max * d_out(v);
- *   - random walks (Alg. 2, lines 5-10): for every v with r(v) > 0,
+ *   - random walks (Alg. 2): for every v with r(v) > 0,
  *     omega_v = ceil(r(v) * omega / r_sum) walks, each adding
  *     a_v * r_sum / omega = r(v) / omega_v to the estimate of its end node.
  *     omega / r_sum is the constant C = (2eps/3+2) log(2/p_f) / (eps^2 delta),
@@ -76,7 +76,7 @@ typedef struct {
 
 /* ---------------------------------------------------------------- params */
 
-/* C = omega / r_sum = (2eps/3 + 2) * log(2/p_f) / (eps^2 * delta)  (Alg. 2, line 3). */
+/* C = omega / r_sum = (2eps/3 + 2) * log(2/p_f) / (eps^2 * delta)  (Alg. 2). */
 double oracle_walk_scale(double eps, double delta, double pf) {
   return ((2.0 * eps / 3.0 + 2.0) * log(2.0 / pf)) / (eps * eps * delta);
 }
@@ -152,7 +152,7 @@ int oracle_forward_push(int64_t n, const int64_t *row_ptr, const int32_t *col, i
   }
   oracle_push_stats local = {0, 0, 0, 0.0};
 
-  /* Alg. 1, lines 1-2 */
+  /* Alg. 1 */
   for (int64_t v = 0; v < n; ++v) { reserve[v] = 0.0; residue[v] = 0.0; }
   residue[s] = 1.0;
 
@@ -252,7 +252,7 @@ static int64_t random_walk(const int64_t *row_ptr, const int32_t *col, uint32_t 
 }
 
 /*
- * Random-walk phase of Alg. 2 (lines 5-10) on a given residue vector:
+ * Random-walk phase of Alg. 2 on a given residue vector:
  * omega_v = ceil(r(v) * C) walks from every v with r(v) > 0, each adding
  * W_v = rint((r(v)/omega_v) * 2^63) to acc[end] and 1 to count[end].
  * count[n] and acc[n] are caller-allocated and overwritten.

@@ -97,7 +97,7 @@ int ensure_workspace(fora_graph* g, Workspace* w, int nsrc) {
   return FORA_OK;
 }
 
-// Parameters as a query resolves them (Alg. 2 line 3; Eq. rmax and Case 2, Section 3.2).
+// Parameters as a query resolves them (Alg. 2; Eq. rmax and Case 2, Section 3.2).
 struct Resolved {
   double alpha, eps, delta, pf, rmax, walk_scale;
   uint32_t alpha_threshold;
@@ -228,7 +228,7 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
   CUDA_TRY(cudaMemsetAsync(w->err, 0, sizeof(uint32_t), stream));
   CUDA_TRY(cudaMemsetAsync(w->stats, 0, nsrc * sizeof(SlotStats), stream));
 
-  GraphDev gd{g->n, g->m, g->row, g->col};
+  const GraphDev gd = g->dev();
   BatchDev b{};
   b.nsrc = nsrc;
   b.alpha = rp.alpha;
@@ -282,7 +282,7 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
   }
   if (timed) CUDA_TRY(cudaEventRecord(w->ev[1], stream));
 
-  // ---- walks (Alg. 2, lines 3-10) ----
+  // ---- walks (Alg. 2) ----
   CUDA_TRY(launch_residuals(gd, b, stream));
   if (timed) CUDA_TRY(cudaEventRecord(w->ev[2], stream));
   CUDA_TRY(launch_walks(gd, b, g->num_sms, stream));
@@ -391,9 +391,28 @@ int fora_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col, uin
   if (e == cudaSuccess) e = cudaMalloc(&g->col, (size_t)m * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemcpy(g->row, row.data(), ((size_t)n + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(g->col, col, (size_t)m * sizeof(int32_t), cudaMemcpyHostToDevice);
+  // walk copy of col: ceil(log2 n) bits per target when that saves at least a quarter
+  int bits = 1;
+  while (bits < 31 && (1ll << bits) < n) ++bits;
+  if (e == cudaSuccess && bits <= 24) {
+    const size_t words = ((size_t)m * bits + 31) / 32 + 2;
+    std::vector<uint32_t> packed(words, 0u);
+    for (int64_t k = 0; k < m; ++k) {
+      const uint64_t bit = (uint64_t)k * bits;
+      const uint64_t w = bit >> 5;
+      const uint32_t off = (uint32_t)(bit & 31);
+      const uint64_t v = (uint64_t)(uint32_t)col[k] << off;
+      packed[w] |= (uint32_t)v;
+      packed[w + 1] |= (uint32_t)(v >> 32);
+    }
+    e = cudaMalloc(&g->colp, words * sizeof(uint32_t));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(g->colp, packed.data(), words * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) g->colbits = bits;
+  }
   if (e == cudaSuccess) e = cudaMalloc(&g->indeg, (size_t)n * sizeof(uint32_t));
   if (e == cudaSuccess) {
-    GraphDev gd{g->n, g->m, g->row, g->col};
+    const GraphDev gd = g->dev();
     e = launch_indegree(gd, g->indeg, g->num_sms, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
   }
@@ -412,6 +431,7 @@ void fora_graph_destroy(fora_graph* g) {
     g->ws.release();
     dfree(g->row);
     dfree(g->col);
+    dfree(g->colp);
     dfree(g->indeg);
   }
   delete g;
@@ -473,7 +493,7 @@ int fora_topk_ssppr_batch(fora_graph* g, const fora_params* params, const int32_
   if (params->flags & (FORA_OUT_DEVICE | FORA_ASYNC))
     return fail(FORA_ERR_BAD_ARG, "top-k FORA writes host outputs and runs synchronously");
   const double n = (double)g->n;
-  // rounds i < I use delta = 1/(k 2^i), round I uses 1/n (Alg. 5, line 1)
+  // rounds i < I use delta = 1/(k 2^i), round I uses 1/n (Alg. 5)
   int32_t last = 0;
   while ((double)k * ldexp(1.0, last) < n) ++last;
   double lg = log2(n / (double)k);
@@ -487,7 +507,7 @@ int fora_topk_ssppr_batch(fora_graph* g, const fora_params* params, const int32_
   std::vector<fora_stats> st(nsrc);
   for (int32_t round = 0; round <= last && !active.empty(); ++round) {
     fora_params pr = *params;
-    pr.eps = params->eps / 2.0;  // eps' = eps / 2 (Alg. 5, line 2)
+    pr.eps = params->eps / 2.0;  // eps' = eps / 2 (Alg. 5)
     pr.delta = round < last ? 1.0 / ((double)k * ldexp(1.0, round)) : 1.0 / n;
     pr.pf = pf_round;
     pr.seed = params->seed + (uint64_t)round;
@@ -500,7 +520,7 @@ int fora_topk_ssppr_batch(fora_graph* g, const fora_params* params, const int32_
     std::vector<int32_t> still;
     for (int i = 0; i < na; ++i) {
       const int j = active[i];
-      // stop once the k-th estimate is at least (1 + eps) delta (Alg. 5, line 4)
+      // stop once the k-th estimate is at least (1 + eps) delta (Alg. 5)
       if (vals[(size_t)i * k + k - 1] >= (1.0 + params->eps) * pr.delta || round == last) {
         memcpy(out_ids + (size_t)j * k, ids.data() + (size_t)i * k, k * sizeof(int32_t));
         memcpy(out_vals + (size_t)j * k, vals.data() + (size_t)i * k, k * sizeof(double));
@@ -773,7 +793,7 @@ int fora_source_features(fora_graph* g, const fora_params* params, const int32_t
   cudaError_t e = cudaMalloc(&d_src, (size_t)nsrc * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&d_out, (size_t)nsrc * FORA_NUM_FEATURES * sizeof(float));
   if (e == cudaSuccess) e = cudaMemcpy(d_src, sources, (size_t)nsrc * sizeof(int32_t), cudaMemcpyHostToDevice);
-  GraphDev gd{g->n, g->m, g->row, g->col};
+  const GraphDev gd = g->dev();
   if (e == cudaSuccess) e = launch_features(gd, g->indeg, d_src, nsrc, rp.alpha, rp.rmax, d_out, 0);
   if (e == cudaSuccess)
     e = cudaMemcpy(out, d_out, (size_t)nsrc * FORA_NUM_FEATURES * sizeof(float), cudaMemcpyDeviceToHost);
@@ -802,7 +822,7 @@ int fora_ssppr_batch_learned(fora_graph* g, const fora_params* params, fora_mode
     if (rc) return rc;
     memcpy(w->h_sources, sources, nsrc * sizeof(int32_t));
     CUDA_TRY(cudaMemcpyAsync(w->sources, w->h_sources, nsrc * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    GraphDev gd{g->n, g->m, g->row, g->col};
+    const GraphDev gd = g->dev();
     // r_rule of these parameters (params->rmax is not used here)
     fora_params pr = *params;
     pr.rmax = 0.0;

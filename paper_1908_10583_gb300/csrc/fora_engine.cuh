@@ -36,7 +36,19 @@ struct GraphDev {
   int64_t m;
   const uint32_t* row;  // [n+1] edge offsets (m < 2^32)
   const int32_t* col;   // [m]
+  // The same targets bit-packed, colbits bits each (0 = not packed), for the walks: a
+  // smaller footprint keeps more of the graph in L2 beside the walk tallies.
+  const uint32_t* colp;
+  int colbits;
 };
+
+// Target e of a bit-packed column array (two 32-bit words always readable).
+__device__ __forceinline__ uint32_t packed_target(const uint32_t* colp, int bits, uint32_t e) {
+  const unsigned long long bit = (unsigned long long)e * (unsigned long long)bits;
+  const unsigned long long w = bit >> 5;
+  const unsigned long long two = (unsigned long long)colp[w] | ((unsigned long long)colp[w + 1] << 32);
+  return (uint32_t)(two >> (bit & 31)) & ((1u << bits) - 1u);
+}
 
 // Walk end tally of one (source, node): fixed-point weight and count share one
 // 16-byte record, so a walk's end touches a single L2 sector.

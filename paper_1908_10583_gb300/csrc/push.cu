@@ -79,7 +79,7 @@ __global__ void k_push_seed(GraphDev g, BatchDev b) {
   for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < b.nsrc;
        slot += gridDim.x * blockDim.x) {
     b.r[(unsigned long long)slot * (unsigned long long)g.n + (uint32_t)b.sources[slot]] = 1.0;
-    // Alg. 1, line 1: r(s) = 1.  The first pass of the loop body has an empty frontier
+    // Alg. 1: r(s) = 1.  The first pass of the loop body has an empty frontier
     // of parity 1 (nothing to spread); its detection scans the sources flagged in
     // active[1] and writes F_0 into q[0].
     b.active[b.nsrc + slot] = 1;

@@ -105,12 +105,15 @@ struct fora_graph {
   uint64_t hub_chunks = 0;  // sum over nodes with d > kHubChunk of ceil(d / kHubChunk)
   uint32_t* row = nullptr;
   int32_t* col = nullptr;
+  uint32_t* colp = nullptr;   // col bit-packed to colbits bits per target (0: not packed)
+  int colbits = 0;
   uint32_t* indeg = nullptr;  // in-degrees (features of the learned r_max)
   int device = 0;
   int num_sms = 0;
   fora::Tuning tune;
   std::mutex mu;              // guards `tune`
   fora::Workspace ws;         // the graph's own entry points
+  fora::GraphDev dev() const { return fora::GraphDev{n, m, row, col, colp, colbits}; }
 };
 
 namespace fora {

@@ -2,9 +2,9 @@
 //
 //   k_residual_count / k_residual_scan / k_residual_emit:
 //     R = {(slot, v) : r(v) > 0} in ascending (slot, v); omega_v = ceil(r(v) * C) with
-//     C = omega / r_sum (Alg. 2 line 3); exclusive offsets of omega_v over R (one flat
+//     C = omega / r_sum (Alg. 2); exclusive offsets of omega_v over R (one flat
 //     walk index space for all sources) and the fixed-point weight
-//     W_v = rint(r(v)/omega_v * 2^63) of every walk from v (Alg. 2 line 7: a_v r_sum/omega).
+//     W_v = rint(r(v)/omega_v * 2^63) of every walk from v (Alg. 2: a_v r_sum/omega).
 //   k_walks:
 //     walk g in [0, W) belongs to the entry i with offset[i] <= g < offset[i+1] and is
 //     walk j = g - offset[i] of node v; it reads its own Philox4x32-10 stream with
@@ -31,35 +31,22 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
   return c;
 }
 
-// The word stream of one walk: blocks c = 0, 1, ... of Philox with counter (c, j, v, s),
-// consumed in order.  Besides the current block a lane may hold the next one
-// (prefetched), so the walk loop can generate blocks for all lanes of a warp at the same
-// point instead of one lane at a time.
+// The word stream of one walk: blocks c = 0, 1, ... of Philox with counter (c, j, v, s).
 struct WalkStream {
   uint32_t c, j, v, s;
   uint2 key;
-  uint32_t w0, w1, w2, w3;  // current block, w0 is the next word
-  int avail;                // words left in the current block
-  uint32_t p0, p1, p2, p3;  // the next block, if pre
-  bool pre;
+  uint32_t w0, w1, w2, w3;
+  int avail;
   __device__ __forceinline__ void reset(uint32_t jj, uint32_t vv, uint32_t ss) {
     c = 0; j = jj; v = vv; s = ss;
     avail = 0;
-    pre = false;
   }
-  __device__ __forceinline__ void prefetch() {
-    const uint4 o = philox4x32_10(make_uint4(c, j, v, s), key);
-    ++c;
-    p0 = o.x; p1 = o.y; p2 = o.z; p3 = o.w;
-    pre = true;
-  }
-  __device__ __forceinline__ int buffered() const { return avail + (pre ? 4 : 0); }
   __device__ __forceinline__ uint32_t next() {
     if (avail == 0) {
-      if (!pre) prefetch();
-      w0 = p0; w1 = p1; w2 = p2; w3 = p3;
+      const uint4 o = philox4x32_10(make_uint4(c, j, v, s), key);
+      ++c;
+      w0 = o.x; w1 = o.y; w2 = o.z; w3 = o.w;
       avail = 4;
-      pre = false;
     }
     const uint32_t r = w0;
     w0 = w1; w1 = w2; w2 = w3;
@@ -290,7 +277,6 @@ __global__ void __launch_bounds__(kWalkThreads, kMinBlocks) k_walks(GraphDev g, 
     bool have = i < cnt;
     WalkStream rng;
     rng.key = key;
-    rng.pre = false;
     rng.avail = 0;
     uint32_t x = 0, slot = 0, steps = 0;
     unsigned long long wgt = 0;
@@ -305,10 +291,6 @@ __global__ void __launch_bounds__(kWalkThreads, kMinBlocks) k_walks(GraphDev g, 
       steps = 0;
     }
     while (have) {
-      // an iteration takes at most two words (stop test, neighbour draw) unless the draw
-      // is rejected; when any lane holds fewer, every lane without a prefetched block
-      // generates one, together
-      if (__any_sync(__activemask(), rng.buffered() < 2) && !rng.pre) rng.prefetch();
       if (!forced && rng.next() < t_alpha) {
         // the walk stops at x (Section 2.1): count it and add its weight (Alg. 2)
         Tally* t = b.tally + (unsigned long long)slot * (unsigned long long)g.n + x;
@@ -349,7 +331,8 @@ __global__ void __launch_bounds__(kWalkThreads, kMinBlocks) k_walks(GraphDev g, 
         }
         if (low < reject_below) { capped = true; have = false; break; }
       }
-      x = (uint32_t)g.col[rb0 + (uint32_t)(m >> 32)];
+      const uint32_t e = rb0 + (uint32_t)(m >> 32);
+      x = g.colbits ? packed_target(g.colp, g.colbits, e) : (uint32_t)g.col[e];
       ++steps;
     }
     __syncwarp();

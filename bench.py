@@ -278,9 +278,9 @@ def run_fora(args):
 
     def collect(step, st, ms):
         rounds = max(s.push_rounds for s in st)
-        # push: the seed, then (rounds + 1) passes of the graph loop body (spread, detect,
-        # scan, emit, advance); residuals 3, walks 1, estimate 1, top-k select 19
-        counters["launches"] += 1 + 5 * (rounds + 1) + 3 + 1 + 1 + 19
+        # push: the seed, then (rounds + 1) passes of the loop body (spread, take,
+        # advance); residuals 3, walks 1, estimate 1, top-k select 19
+        counters["launches"] += 1 + 3 * (rounds + 1) + 3 + 1 + 1 + 19
         if model is not None:
             counters["launches"] += 3  # features, forward, r_max
         for key in phase:
@@ -318,27 +318,29 @@ def run_fora(args):
     if mode == "learned":
         rule_ms = timed(None, args.steps)
         comparison["batched_rule_qps"] = B * args.steps / (sum(rule_ms) / 1e3)
-    plain_src = inputs.uniform_sources(n, args.plain_sources, inputs.SOURCE_SEED + 31337)
-    h_ids1 = np.zeros(k, dtype=np.int32)
-    g.ssppr(int(plain_src[0]), params)  # warm the single-source workspace
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for s_ in plain_src:
-        g.ssppr(int(s_), params)
-    comparison["plain_fora_qps"] = len(plain_src) / (time.perf_counter() - t0)
-    del h_ids1
+    if args.plain_sources > 0:
+        plain_src = inputs.uniform_sources(n, args.plain_sources, inputs.SOURCE_SEED + 31337)
+        g.ssppr(int(plain_src[0]), params)  # warm the single-source workspace
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s_ in plain_src:
+            g.ssppr(int(s_), params)
+        comparison["plain_fora_qps"] = len(plain_src) / (time.perf_counter() - t0)
 
     # end to end through the public API: host sources in, host results out
     h_ids = torch.empty((B, k), dtype=torch.int32, pin_memory=True).numpy()
     h_vals = torch.empty((B, k), dtype=torch.float64, pin_memory=True).numpy()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for step in range(args.steps):
+    e2e_s = 0.0
+    for step in range(args.steps):  # the timed steps' sources, L2 flushed before each
+        src = sources(step)
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         if model is not None:
-            g.ssppr_batch_learned(sources(10_000 + step), params, model, stream=stream)
+            g.ssppr_batch_learned(src, params, model, stream=stream)
         else:
-            g.ssppr_batch_host(sources(10_000 + step), params, h_ids, h_vals, stream=stream)
-    e2e_s = time.perf_counter() - t0
+            g.ssppr_batch_host(src, params, h_ids, h_vals, stream=stream)
+        e2e_s += time.perf_counter() - t0
     e2e = {"value": B * args.steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": B * (4 + 8),
            "d2h_bytes_per_step": B * k * (4 + 8)}

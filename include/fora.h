@@ -336,6 +336,11 @@ int fora_philox_debug(const uint32_t *ctr_key, uint32_t *out, int32_t count);
  * many sources at once (wider spreads reductions on shared hub targets over more
  * addresses; narrower keeps the residue arrays in flight smaller).  "walk_blocks" (4, 5
  * or 6, default 4): resident walk blocks per SM, traded against registers per thread.
+ * "push_host_loop" (0 or 1, default 0): 1 launches the push rounds from a host loop with
+ * one device-to-host read per round, instead of the CUDA graph whose conditional while-node
+ * runs them on the device; the kernels are the same (a profiler that cannot look inside
+ * conditional graph nodes sees each of them).  Unknown keys and out-of-range values
+ * return FORA_ERR_BAD_ARG.
  */
 int fora_graph_tune(fora_graph *g, const char *key, int64_t value);
 

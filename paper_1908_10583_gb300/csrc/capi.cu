@@ -58,6 +58,10 @@ int ensure_workspace(fora_graph* g, Workspace* w, int nsrc) {
   w->release();
   const size_t N = (size_t)nsrc * (size_t)g->n;
   const size_t H = (size_t)nsrc * g->hub_chunks + 1;
+  // hub items hold a queue index in their upper 64 - kHubChunkBits bits
+  if (N >= (1ull << (64 - kHubChunkBits)))
+    return fail(FORA_ERR_BAD_ARG, "%d sources x %lld nodes exceed the queue index range", nsrc,
+                (long long)g->n);
   w->residual_grid = g->num_sms * 8;
   CUDA_TRY(cudaMalloc(&w->r, N * sizeof(double)));
   CUDA_TRY(cudaMalloc(&w->res, N * sizeof(double)));
@@ -68,10 +72,10 @@ int ensure_workspace(fora_graph* g, Workspace* w, int nsrc) {
   CUDA_TRY(cudaMalloc(&w->hub[0], H * sizeof(unsigned long long)));
   CUDA_TRY(cudaMalloc(&w->hub[1], H * sizeof(unsigned long long)));
   CUDA_TRY(cudaMalloc(&w->small, 8 * sizeof(unsigned long long)));
-  CUDA_TRY(cudaMalloc(&w->mask, (size_t)nsrc * (((size_t)g->n + 31) / 32) * sizeof(uint32_t)));
-  CUDA_TRY(cudaMalloc(&w->hubw, (size_t)nsrc * (((size_t)g->n + 31) / 32) * sizeof(uint32_t)));
   CUDA_TRY(cudaMalloc(&w->work, 32 * sizeof(unsigned long long)));
-  CUDA_TRY(cudaMalloc(&w->active, 2 * (size_t)nsrc * sizeof(uint32_t)));
+  CUDA_TRY(cudaMalloc(&w->alist, (size_t)nsrc * sizeof(uint32_t)));
+  CUDA_TRY(cudaMalloc(&w->slot_cnt, 4 * (size_t)nsrc * sizeof(uint32_t)));
+  CUDA_TRY(cudaMalloc(&w->pre, 2 * ((size_t)nsrc + 1) * sizeof(unsigned long long)));
   CUDA_TRY(cudaMalloc(&w->ps, sizeof(PushState)));
   if (!w->capture_stream) CUDA_TRY(cudaStreamCreateWithFlags(&w->capture_stream, cudaStreamNonBlocking));
   CUDA_TRY(cudaMalloc(&w->err, sizeof(uint32_t)));
@@ -90,6 +94,7 @@ int ensure_workspace(fora_graph* g, Workspace* w, int nsrc) {
   CUDA_TRY(cudaMallocHost(&w->h_err, sizeof(uint32_t)));
   CUDA_TRY(cudaMallocHost(&w->h_sources, nsrc * sizeof(int32_t)));
   CUDA_TRY(cudaMallocHost(&w->h_rmax, nsrc * sizeof(double)));
+  CUDA_TRY(cudaMallocHost(&w->go_host, sizeof(uint32_t)));
   for (int i = 0; i < 5; ++i)
     if (!w->ev[i]) CUDA_TRY(cudaEventCreate(&w->ev[i]));
   w->cap = nsrc;
@@ -164,7 +169,7 @@ int push_loop_graph(fora_graph* g, Workspace* w, const GraphDev& gd, const Batch
     e = cudaStreamBeginCaptureToGraph(w->capture_stream, np.conditional.phGraph_out[0], nullptr,
                                       nullptr, 0, cudaStreamCaptureModeRelaxed);
   if (e == cudaSuccess) {
-    const cudaError_t le = launch_push_body(gd, b, g->num_sms, loop, w->capture_stream);
+    const cudaError_t le = launch_push_body(gd, b, g->num_sms, loop, true, w->capture_stream);
     e = cudaStreamEndCapture(w->capture_stream, &captured);
     if (le != cudaSuccess) e = le;
   }
@@ -239,11 +244,12 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
   b.r = w->r; b.res = w->res; b.tally = w->tally;
   b.q[0] = w->q[0]; b.q[1] = w->q[1]; b.fa = w->fa;
   b.hub[0] = w->hub[0]; b.hub[1] = w->hub[1];
-  b.counters = w->small;
-  b.mask = w->mask;
-  b.hubw = w->hubw;
+  b.hub_stride = g->hub_chunks;
+  b.slot_cnt = w->slot_cnt;
+  b.gpre = w->pre;
+  b.hpre = w->pre + (nsrc + 1);
+  b.alist = w->alist;
   b.work = w->work;
-  b.active = w->active;
   b.ps = w->ps;
   b.totals = w->small + 4;
   b.sources = w->sources; b.rmax = w->rmax; b.stats = w->stats; b.err = w->err;
@@ -270,11 +276,25 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
     CUDA_TRY(cudaMemsetAsync(w->r, 0, N * sizeof(double), stream));
     CUDA_TRY(cudaMemsetAsync(w->res, 0, N * sizeof(double), stream));
     CUDA_TRY(cudaMemsetAsync(w->work, 0, 32 * sizeof(unsigned long long), stream));
+    CUDA_TRY(cudaMemsetAsync(w->slot_cnt, 0, 4 * (size_t)nsrc * sizeof(uint32_t), stream));
     CUDA_TRY(launch_push_seed(gd, b, stream));
-    // the rounds run as a device-side while loop (no host round trip per round)
-    rc = push_loop_graph(g, w, gd, b);
-    if (rc) return rc;
-    CUDA_TRY(cudaGraphLaunch(w->push_exec, stream));
+    if (g->tune.push_host_loop) {
+      // the same round kernels launched one round at a time from the host (for profilers
+      // that cannot look inside conditional graph nodes); one host round trip per round
+      uint32_t go = 1;
+      while (go) {
+        CUDA_TRY(launch_push_body(gd, b, g->num_sms, 0, false, stream));
+        CUDA_TRY(cudaMemcpyAsync(w->go_host, &w->ps->go, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                 stream));
+        CUDA_TRY(cudaStreamSynchronize(stream));
+        go = *w->go_host;
+      }
+    } else {
+      // the rounds run as a device-side while loop (no host round trip per round)
+      rc = push_loop_graph(g, w, gd, b);
+      if (rc) return rc;
+      CUDA_TRY(cudaGraphLaunch(w->push_exec, stream));
+    }
     if (dbg && dbg->reserve)
       CUDA_TRY(cudaMemcpyAsync(dbg->reserve, w->res, N * sizeof(double), cudaMemcpyDeviceToDevice, stream));
     if (dbg && dbg->residue)
@@ -581,6 +601,11 @@ int fora_graph_tune(fora_graph* g, const char* key, int64_t value) {
   if (strcmp(key, "walk_blocks") == 0) {
     if (value < 4 || value > 6) return fail(FORA_ERR_BAD_ARG, "walk_blocks must be 4, 5 or 6");
     g->tune.walk_blocks = (int)value;
+    return FORA_OK;
+  }
+  if (strcmp(key, "push_host_loop") == 0) {
+    if (value != 0 && value != 1) return fail(FORA_ERR_BAD_ARG, "push_host_loop must be 0 or 1");
+    g->tune.push_host_loop = (int)value;
     return FORA_OK;
   }
   return fail(FORA_ERR_BAD_ARG, "unknown tuning key '%s'", key);

@@ -24,11 +24,16 @@ constexpr uint32_t kErrWalkOverflow = 2u;
 constexpr uint32_t kErrPushNotConverged = 4u;
 constexpr uint32_t kMaxPushRounds = 100000u;
 
-// Where the push loop stands: the parity of the current frontier queue and the number
-// of rounds done.  Kept on the device so the loop runs without the host.
+// Where the push loop stands: the parity of the current frontier queue, the number of
+// rounds done, and the shape of the current frontier.  Kept on the device so the loop
+// runs without the host.
 struct PushState {
   int cur;
   uint32_t round;
+  uint32_t go;    // the loop condition of the last round (read by the host-driven loop)
+  uint32_t nact;  // sources with a non-empty current frontier (listed in BatchDev::alist)
+  unsigned long long ngroups;  // 32-entry groups of the current frontier, over all sources
+  unsigned long long nhub;     // hub items of the current frontier, over all sources
 };
 
 struct GraphDev {
@@ -92,14 +97,18 @@ struct BatchDev {
   double* r;                 // residue, later the estimate
   double* res;               // reserve
   Tally* tally;              // walk ends per (source, node)
-  unsigned long long* q[2];  // frontier queues: (slot << 32) | v
+  // Frontier of source `slot`: entries (slot << 32) | v at q[par][slot * n + j],
+  // j < slot_cnt[par][slot], with increments fa[slot * n + j]; its hub items at
+  // hub[par][slot * hub_stride + j], j < slot_cnt[2 + par][slot].
+  unsigned long long* q[2];
   double* fa;                // per frontier entry: (1 - alpha) r(v) / d(v)
-  unsigned long long* hub[2];  // hub chunk items
-  unsigned long long* counters;  // [4]: frontier/hub counts of parity 0 and 1
-  uint32_t* mask;            // crossing mask, one bit per (slot, node), rows padded to words
-  uint32_t* hubw;            // hub items of the crossing nodes of each mask word
+  unsigned long long* hub[2];  // hub chunk items: (q index << kHubChunkBits) | chunk
+  unsigned long long hub_stride;
+  uint32_t* slot_cnt;        // [4][nsrc]: entries of parity 0, 1; hub items of parity 0, 1
+  unsigned long long* gpre;  // [nsrc + 1]: exclusive prefix of ceil(entries / 32), current
+  unsigned long long* hpre;  // [nsrc + 1]: exclusive prefix of hub items, current
+  uint32_t* alist;           // [nsrc]: the sources with a non-empty current frontier
   unsigned long long* work;  // dynamic work counters of the spread ([0] and [16])
-  uint32_t* active;          // [2][nsrc]: sources with entries in q[0] / q[1]
   PushState* ps;
   const int32_t* sources;    // [nsrc]
   const double* rmax;        // [nsrc]
@@ -121,16 +130,18 @@ struct BatchDev {
 struct Tuning {
   int spread_width = 1;
   int walk_blocks = 4;
+  int push_host_loop = 0;  // 1: rounds launched from a host loop instead of the graph
 };
 
 // capi.cu: record a failure for fora_last_error() and return `code`.
 int report_error(int code, const char* fmt, ...);
 
 // push.cu: r(s) = 1 and the loop state; then the rounds, each launched by the body of a
-// conditional while-node of a CUDA graph (the body sets the loop condition itself).
+// conditional while-node of a CUDA graph (the body sets the loop condition itself), or,
+// with in_graph false, from a host loop that reads PushState::go after each round.
 cudaError_t launch_push_seed(const GraphDev& g, const BatchDev& b, cudaStream_t st);
 cudaError_t launch_push_body(const GraphDev& g, const BatchDev& b, int num_sms,
-                             cudaGraphConditionalHandle loop, cudaStream_t st);
+                             cudaGraphConditionalHandle loop, bool in_graph, cudaStream_t st);
 
 // walk.cu
 cudaError_t launch_residuals(const GraphDev& g, const BatchDev& b, cudaStream_t st);

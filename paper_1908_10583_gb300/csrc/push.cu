@@ -1,25 +1,27 @@
 // Forward Push (Alg. 1) as synchronous frontier rounds over a batch of sources.
 //
-// F_t holds the pairs (slot, v) with r(v) > r_max * d(v), sorted by (slot, v), and for
-// each entry the increment inc_v = (1 - alpha) a_v / d(v) of its taken residue a_v.
-// Round t:
+// F_t holds, per source, the nodes v with r(v) > r_max * d(v) at the start of round t,
+// each with the increment inc_v = (1 - alpha) a_v / d(v) of its taken residue a_v.
+// Source s keeps its part of F_t in its own region of the queue (q[par][s * n + j]), so
+// the frontier is grouped by source without a global sort.  Round t:
 //   k_push_spread   r(u) += inc_v for every out-edge (v, u) of F_t: FP64 reductions
 //                   that return nothing, so a warp never waits on an atomic.
-//   k_push_detect   F_{t+1} = {u : r(u) > r_max * d(u)} over the sources that pushed in
-//                   round t (every other r is unchanged and below its threshold): one
-//                   pass marks the crossing nodes in a bit mask and counts them per block,
-//   k_push_scan     one block turns the per-block counts into output offsets,
-//   k_push_emit     a second pass writes F_{t+1} in (slot, v) order and takes each new
-//                   node's residue: a_u = r(u); reserve(u) += alpha a_u; r(u) = 0;
+//   k_push_take     F_{t+1} = {u : r(u) > r_max * d(u)} over the sources that pushed in
+//                   round t (every other r is unchanged and below its threshold), in one
+//                   streaming pass over their residues; each crossing node is appended
+//                   to its source's region and taken at once:
+//                   a_u = r(u); reserve(u) += alpha a_u; r(u) = 0;
 //                   inc_u = (1 - alpha) a_u / d(u)   (the first half of round t+1).
+//   k_push_advance  one block: per-source prefix of the new frontier's groups and hub
+//                   items, the list of sources still pushing, the loop condition.
 // The take of round t+1 happens after every add of round t (kernel boundary), so
 // residue arriving at a frontier node during a round waits for the next round.
 //
 // Spread load balance: a warp takes 32 frontier entries with d <= kHubChunk, scans their
 // degrees and walks their concatenated edge lists 128 edges per iteration (coalesced
 // col reads); nodes with more out-edges are split into kHubChunk-edge hub items, one
-// warp each.  Sorted frontiers keep the warps in flight on a few sources at a time, so
-// the residue arrays they add into stay in L2.
+// warp each.  Work is handed out in source order, so the warps in flight work on a few
+// sources at a time and the residue arrays they add into stay in L2.
 #include "fora_engine.cuh"
 
 namespace fora {
@@ -27,8 +29,9 @@ namespace fora {
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr int kDetectThreads = 256;
+constexpr int kTakeThreads = 256;
 constexpr int kSpreadThreads = 256;
+constexpr uint32_t kTileNodes = 1024;  // nodes of one source a warp scans per take tile
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
@@ -70,45 +73,59 @@ __device__ __forceinline__ uint32_t hub_chunks_of(uint32_t d) {
   return d > kHubChunk ? (d + kHubChunk - 1) / kHubChunk : 0u;
 }
 
-// Words of the crossing mask: one bit per (slot, node), each slot padded to whole words.
-__device__ __forceinline__ unsigned long long words_per_slot(int64_t n) {
-  return ((unsigned long long)n + 31) / 32;
+// The source whose range [pre[s], pre[s + 1]) holds x, for a non-decreasing prefix with
+// x < pre[nsrc]: the largest s with pre[s] <= x (empty sources have pre[s] = pre[s + 1]).
+__device__ __forceinline__ int slot_of(const unsigned long long* pre, int nsrc,
+                                       unsigned long long x) {
+  int lo = 0, hi = nsrc - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
 }
 
 __global__ void k_push_seed(GraphDev g, BatchDev b) {
   for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < b.nsrc;
        slot += gridDim.x * blockDim.x) {
+    // Alg. 1 starts from r(s) = 1.  The first pass of the loop body has an empty
+    // frontier (nothing to spread); its take scans every source and finds F_0.
     b.r[(unsigned long long)slot * (unsigned long long)g.n + (uint32_t)b.sources[slot]] = 1.0;
-    // Alg. 1: r(s) = 1.  The first pass of the loop body has an empty frontier
-    // of parity 1 (nothing to spread); its detection scans the sources flagged in
-    // active[1] and writes F_0 into q[0].
-    b.active[b.nsrc + slot] = 1;
+    b.alist[slot] = (uint32_t)slot;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    b.ps->cur = 1;
-    b.ps->round = 0;
+    PushState* ps = b.ps;
+    ps->cur = 1;
+    ps->round = 0;
+    ps->go = 1;
+    ps->nact = (uint32_t)b.nsrc;
+    ps->ngroups = 0;
+    ps->nhub = 0;
   }
 }
 
 // Work is handed out dynamically (kGrab groups or hub items per atomic), so the warps
-// in flight always hold the next unprocessed stretch of the sorted frontier, whatever
-// the cost of each group.
+// in flight always hold the next unprocessed stretch of the frontier, whatever the cost
+// of each group.
 constexpr unsigned long long kGrab = 4;
 
 __global__ void __launch_bounds__(kSpreadThreads) k_push_spread(GraphDev g, BatchDev b) {
   const int cur = b.ps->cur;
-  const unsigned long long nf = b.counters[cur * 2];
-  const unsigned long long nh = b.counters[cur * 2 + 1];
+  const unsigned long long ngroups = b.ps->ngroups;
+  const unsigned long long nh = b.ps->nhub;
   const unsigned long long* q = b.q[cur];
+  const uint32_t* cnt = b.slot_cnt + (size_t)cur * b.nsrc;
   const uint32_t lane = lane_id();
   const unsigned long long n = (unsigned long long)g.n;
 
-  // groups of 32 frontier entries (nodes with d <= kHubChunk), visited through
-  // b.spread_width interleaved segments of the sorted frontier
-  const unsigned long long ngroups = (nf + 31) / 32;
+  // groups of 32 frontier entries of one source (nodes with d <= kHubChunk), visited
+  // through b.spread_width interleaved segments of the frontier
   const unsigned long long width = (unsigned long long)b.spread_width;
   const unsigned long long gseg = (ngroups + width - 1) / width;
   const unsigned long long gtotal = gseg * width;
+  int cs = 0;                           // source of the cached range
+  unsigned long long clo = 1, chi = 0;  // its groups [clo, chi) (empty: nothing cached)
+  uint32_t ccnt = 0;
   for (;;) {
     unsigned long long v0 = 0;
     if (lane == 0) v0 = atomicAdd(&b.work[0], kGrab);
@@ -118,27 +135,30 @@ __global__ void __launch_bounds__(kSpreadThreads) k_push_spread(GraphDev g, Batc
     for (unsigned long long vg = v0; vg < v1; ++vg) {
       const unsigned long long grp = (vg % width) * gseg + vg / width;
       if (grp >= ngroups) continue;
-      const unsigned long long i = grp * 32 + lane;
-      uint32_t cnt = 0, rb = 0;
-      unsigned long long base_gi = 0;  // slot * n
+      if (grp < clo || grp >= chi) {  // warp-uniform
+        cs = slot_of(b.gpre, b.nsrc, grp);
+        clo = b.gpre[cs];
+        chi = b.gpre[cs + 1];
+        ccnt = cnt[cs];
+      }
+      const uint32_t i = (uint32_t)(grp - clo) * 32u + lane;
+      const unsigned long long base_gi = (unsigned long long)cs * n;
+      uint32_t c = 0, rb = 0;
       double inc = 0.0;
-      if (i < nf) {
-        const unsigned long long e = q[i];
-        const uint32_t v = (uint32_t)e;
-        base_gi = (e >> 32) * n;
+      if (i < ccnt) {
+        const uint32_t v = (uint32_t)q[base_gi + i];
         rb = g.row[v];
         const uint32_t d = g.row[v + 1] - rb;
         if (d <= kHubChunk) {
-          cnt = d;
-          inc = b.fa[i];
+          c = d;
+          inc = b.fa[base_gi + i];
         }
       }
-      const uint32_t incl = warp_incl_scan(cnt);
+      const uint32_t incl = warp_incl_scan(c);
       const uint32_t total = __shfl_sync(kFull, incl, 31);
-      const uint32_t excl = incl - cnt;
+      const uint32_t excl = incl - c;
       for (uint32_t base = 0; base < total; base += 128) {
         uint32_t u[4];
-        unsigned long long gb[4];
         double ik[4];
         bool act[4];
 #pragma unroll
@@ -152,14 +172,13 @@ __global__ void __launch_bounds__(kSpreadThreads) k_push_spread(GraphDev g, Batc
           }
           const uint32_t ek = __shfl_sync(kFull, excl, lo);
           const uint32_t rbk = __shfl_sync(kFull, rb, lo);
-          gb[k] = __shfl_sync(kFull, base_gi, lo);
           ik[k] = __shfl_sync(kFull, inc, lo);
           act[k] = e < total;
           u[k] = act[k] ? (uint32_t)g.col[rbk + (e - ek)] : 0u;
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-          if (act[k]) atomicAdd(&b.r[gb[k] + u[k]], ik[k]);
+          if (act[k]) atomicAdd(&b.r[base_gi + u[k]], ik[k]);
       }
     }
   }
@@ -167,6 +186,8 @@ __global__ void __launch_bounds__(kSpreadThreads) k_push_spread(GraphDev g, Batc
   // hub items: kHubChunk edges of one frontier node each, same segment order
   const unsigned long long hseg = (nh + width - 1) / width;
   const unsigned long long htotal = hseg * width;
+  clo = 1;
+  chi = 0;
   for (;;) {
     unsigned long long v0 = 0;
     if (lane == 0) v0 = atomicAdd(&b.work[16], kGrab);
@@ -176,12 +197,17 @@ __global__ void __launch_bounds__(kSpreadThreads) k_push_spread(GraphDev g, Batc
     for (unsigned long long vh = v0; vh < v1; ++vh) {
       const unsigned long long h = (vh % width) * hseg + vh / width;
       if (h >= nh) continue;
-      const unsigned long long item = b.hub[cur][h];
+      if (h < clo || h >= chi) {  // warp-uniform
+        cs = slot_of(b.hpre, b.nsrc, h);
+        clo = b.hpre[cs];
+        chi = b.hpre[cs + 1];
+      }
+      const unsigned long long item =
+          b.hub[cur][(unsigned long long)cs * b.hub_stride + (h - clo)];
       const unsigned long long fi = item >> kHubChunkBits;
       const uint32_t c = (uint32_t)(item & ((1ull << kHubChunkBits) - 1));
-      const unsigned long long e = q[fi];
-      const uint32_t v = (uint32_t)e;
-      const unsigned long long gbase = (e >> 32) * n;
+      const uint32_t v = (uint32_t)q[fi];
+      const unsigned long long gbase = (unsigned long long)cs * n;
       const uint32_t rb = g.row[v], re = g.row[v + 1];
       const double inc = b.fa[fi];
       const uint32_t beg = rb + c * kHubChunk;
@@ -199,227 +225,188 @@ __global__ void __launch_bounds__(kSpreadThreads) k_push_spread(GraphDev g, Batc
   }
 }
 
-// Element range (in mask words) of block `blk`.
-__device__ __forceinline__ void word_range(unsigned long long total, int blk, int nblk,
-                                           unsigned long long* beg, unsigned long long* end) {
-  *beg = total * (unsigned long long)blk / (unsigned long long)nblk;
-  *end = total * (unsigned long long)(blk + 1) / (unsigned long long)nblk;
-}
-
-// Pass 1: crossing mask, per-word hub-item counts and per-block counts (nodes, hub
-// items) over the active slots.  A warp takes 32 mask words (1024 nodes, slot rows
-// padded to whole words) at a time; for word k the 32 lanes test 32 consecutive nodes
-// and the ballot of their tests is the mask word.  Eight words' residues are loaded
-// before any is used.
-__global__ void __launch_bounds__(kDetectThreads) k_push_detect(GraphDev g, BatchDev b) {
-  const int par = b.ps->cur;
-  const unsigned long long wps = words_per_slot(g.n);
-  const unsigned long long total = (unsigned long long)b.nsrc * wps;
-  unsigned long long wbeg, wend;
-  word_range(total, blockIdx.x, gridDim.x, &wbeg, &wend);
-  const uint32_t* act = b.active + (size_t)par * b.nsrc;
-  if (blockIdx.x == 0) {  // flags of the next frontier: set by the emit pass
-    uint32_t* nxt = b.active + (size_t)(par ^ 1) * b.nsrc;
-    for (int s = threadIdx.x; s < b.nsrc; s += blockDim.x) nxt[s] = 0;
-  }
-  const uint32_t lane = lane_id();
-  const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+// Detection and take of the next frontier in one pass.  Warp w scans tiles w, w + W, ...
+// of kTileNodes nodes of one pushing source; for 8 words of 32 nodes at a time the
+// residues and both row offsets are loaded before any is used, the crossing nodes of
+// the 8 words are counted, one atomic per counter reserves their places in the source's
+// queue region, and the crossing nodes are taken.
+__global__ void __launch_bounds__(kTakeThreads, 3) k_push_take(GraphDev g, BatchDev b) {
+  const PushState* ps = b.ps;
+  const int nx = ps->cur ^ 1;
+  const uint32_t round = ps->round + 1;  // the take done here belongs to the next round
   const unsigned long long n = (unsigned long long)g.n;
-  unsigned long long nodes = 0, hubs = 0;
-  for (unsigned long long gw = wbeg + 32ull * wid; gw < wend; gw += 32ull * nw) {
-    unsigned long long slot = gw / wps;
-    // words of sources that did not push are neither scanned nor written
-    if (!act[slot] && gw + 32 <= (slot + 1) * wps) continue;
-    uint32_t my_mask = 0, my_hubs = 0;
-    for (int k0 = 0; k0 < 32; k0 += 8) {
-      double rv[8];
-      uint32_t uu[8];
-      unsigned long long ss[8];
-#pragma unroll
-      for (int kk = 0; kk < 8; ++kk) {
-        const unsigned long long w = gw + k0 + kk;
-        while (w >= (slot + 1) * wps) ++slot;
-        ss[kk] = slot;
-        uu[kk] = (uint32_t)((w - slot * wps) * 32) + lane;
-        const bool ok = w < wend && slot < (unsigned long long)b.nsrc && act[slot] && uu[kk] < n;
-        rv[kk] = ok ? b.r[slot * n + uu[kk]] : 0.0;
-      }
-#pragma unroll
-      for (int kk = 0; kk < 8; ++kk) {
-        bool cross = false;
-        uint32_t h = 0;
-        if (rv[kk] > 0.0) {
-          const uint32_t d = g.row[uu[kk] + 1] - g.row[uu[kk]];
-          if (rv[kk] > __dmul_rn(b.rmax[ss[kk]], (double)d)) {
-            cross = true;
-            h = hub_chunks_of(d);
-          }
-        }
-        const uint32_t m = __ballot_sync(kFull, cross);
-        const uint32_t hw = __reduce_add_sync(kFull, h);
-        if ((int)lane == k0 + kk) { my_mask = m; my_hubs = hw; }
-        nodes += cross ? 1 : 0;
-        hubs += h;
-      }
-    }
-    const unsigned long long w = gw + lane;
-    if (w < wend && act[w / wps]) {
-      b.mask[w] = my_mask;
-      b.hubw[w] = my_hubs;
-    }
-  }
-  unsigned long long ne, he, nt, ht;
-  block_scan2(nodes, hubs, &ne, &he, &nt, &ht);
-  if (threadIdx.x == 0) {
-    b.blk_cnt[blockIdx.x] = nt;
-    b.blk_walks[blockIdx.x] = ht;
-  }
-}
-
-// One block: exclusive scan of the per-block counts; totals into the next counters.
-__global__ void __launch_bounds__(1024) k_push_scan(BatchDev b) {
-  const int nxt = b.ps->cur ^ 1;
-  __shared__ unsigned long long carry_n, carry_h;
-  if (threadIdx.x == 0) { carry_n = 0; carry_h = 0; }
-  __syncthreads();
-  for (int base = 0; base < b.residual_grid; base += blockDim.x) {
-    const int i = base + threadIdx.x;
-    const unsigned long long c = i < b.residual_grid ? b.blk_cnt[i] : 0;
-    const unsigned long long h = i < b.residual_grid ? b.blk_walks[i] : 0;
-    unsigned long long ce, he, ct, ht;
-    block_scan2(c, h, &ce, &he, &ct, &ht);
-    if (i < b.residual_grid) {
-      b.blk_cnt[i] = carry_n + ce;
-      b.blk_walks[i] = carry_h + he;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) { carry_n += ct; carry_h += ht; }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    b.counters[nxt * 2] = carry_n;
-    b.counters[nxt * 2 + 1] = carry_h;
-    b.work[0] = 0;   // dynamic work counters of the next spread
-    b.work[16] = 0;
-  }
-}
-
-// Pass 2: write F_{t+1} in order and take the residue of its nodes.  The block walks its
-// word range in tiles of 32 words per warp; within a word the lanes are the 32 bits, so
-// the residue, reserve and degree reads and the frontier writes are coalesced.
-__global__ void __launch_bounds__(kDetectThreads) k_push_emit(GraphDev g, BatchDev b) {
-  const int par = b.ps->cur;
-  const uint32_t round = b.ps->round + 1;  // the take done here belongs to the next round
-  const int nxt = par ^ 1;
-  const unsigned long long wps = words_per_slot(g.n);
-  const unsigned long long total = (unsigned long long)b.nsrc * wps;
-  unsigned long long wbeg, wend;
-  word_range(total, blockIdx.x, gridDim.x, &wbeg, &wend);
-  const uint32_t* act = b.active + (size_t)par * b.nsrc;
-  uint32_t* act_next = b.active + (size_t)nxt * b.nsrc;
+  const unsigned long long tps = (n + kTileNodes - 1) / kTileNodes;
+  const unsigned long long ntiles = (unsigned long long)ps->nact * tps;
+  uint32_t* cnt_nx = b.slot_cnt + (size_t)nx * b.nsrc;
+  uint32_t* hcnt_nx = b.slot_cnt + (size_t)(2 + nx) * b.nsrc;
+  unsigned long long* qn = b.q[nx];
+  unsigned long long* hn = b.hub[nx];
   const double alpha = b.alpha, beta = __dadd_rn(1.0, -b.alpha);
   const uint32_t lane = lane_id();
   const uint32_t lt_mask = (1u << lane) - 1u;
-  const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const unsigned long long n = (unsigned long long)g.n;
-  unsigned long long pos = b.blk_cnt[blockIdx.x];
-  unsigned long long hpos = b.blk_walks[blockIdx.x];
-  for (unsigned long long tile = wbeg; tile < wend; tile += 32ull * nw) {
-    const unsigned long long gw = tile + 32ull * wid;  // this warp's 32 words
-    const unsigned long long w = gw + lane;
-    uint32_t my_mask = 0, hubs = 0;
-    if (w < wend && act[w / wps]) {
-      my_mask = b.mask[w];
-      if (my_mask) hubs = b.hubw[w];
-    }
-    const uint32_t nodes = __popc(my_mask);
-    unsigned long long slot;
-    unsigned long long ne, he, nt, ht;
-    const unsigned long long wn = __reduce_add_sync(kFull, nodes);
-    const unsigned long long wh = __reduce_add_sync(kFull, hubs);
-    block_scan2(lane == 0 ? wn : 0, lane == 0 ? wh : 0, &ne, &he, &nt, &ht);
-    unsigned long long p = pos + __shfl_sync(kFull, ne, 0);
-    unsigned long long hp = hpos + __shfl_sync(kFull, he, 0);
-    slot = gw / wps;
-    uint32_t dsum = 0, cnt_slot = 0;
-    for (int k0 = 0; k0 < 32; k0 += 4) {
-      uint32_t m[4], u[4], d[4];
-      unsigned long long sl[4];
-      double a[4], rs[4];
-      uint32_t any = 0;
-      unsigned long long s_it = slot;
+  const unsigned long long wpb = blockDim.x >> 5;
+  const unsigned long long nwarps = (unsigned long long)gridDim.x * wpb;
+  for (unsigned long long t = blockIdx.x * wpb + (threadIdx.x >> 5); t < ntiles; t += nwarps) {
+    const uint32_t s = b.alist[t / tps];
+    const uint32_t tb = (uint32_t)((t % tps) * kTileNodes);
+    const double rm = b.rmax[s];
+    const unsigned long long g0 = (unsigned long long)s * n;
+    uint32_t t_cnt = 0;
+    unsigned long long t_d = 0;
+#pragma unroll 1
+    for (uint32_t k0 = 0; k0 < kTileNodes / 32; k0 += 8) {
+      // 256 consecutive nodes: residues and row offsets (nodes past n read row[n], so
+      // their degree is 0) loaded before any is used; the row offset that ends the last
+      // node of a word is the next lane's, and for lane 31 the next word's first
+      const uint32_t ub = tb + k0 * 32;
+      double rv[8];
+      uint32_t d[8];
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {  // issue every load of four words first
-        m[kk] = __shfl_sync(kFull, my_mask, k0 + kk);
+      for (int kk = 0; kk < 8; ++kk) {
+        const uint32_t u = ub + kk * 32 + lane;
+        rv[kk] = u < n ? b.r[g0 + u] : 0.0;
+        d[kk] = g.row[min((unsigned long long)u, n)];
+      }
+      const uint32_t tail = g.row[min((unsigned long long)(ub + 256), n)];
+      uint32_t m[8], any = 0, mine = 0, my_h = 0, my_d = 0;
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {
+        const uint32_t first_next = kk < 7 ? __shfl_sync(kFull, d[kk + 1], 0) : tail;
+        const uint32_t down = __shfl_down_sync(kFull, d[kk], 1);
+        d[kk] = (lane < 31 ? down : first_next) - d[kk];
+      }
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {
+        const bool cross = rv[kk] > __dmul_rn(rm, (double)d[kk]);
+        m[kk] = __ballot_sync(kFull, cross);
         any |= m[kk];
-        const unsigned long long wk = gw + k0 + kk;
-        while (wk >= (s_it + 1) * wps) ++s_it;
-        sl[kk] = s_it;
-        u[kk] = (uint32_t)((wk - s_it * wps) * 32) + lane;
-        const bool bit = (m[kk] >> lane) & 1u;
-        d[kk] = 0; a[kk] = 0.0; rs[kk] = 0.0;
-        if (bit) {
-          const unsigned long long gi = s_it * n + u[kk];
-          d[kk] = g.row[u[kk] + 1] - g.row[u[kk]];
-          a[kk] = b.r[gi];
-          rs[kk] = b.res[gi];
+        mine += __popc(m[kk]);
+        if (cross) {
+          my_h += hub_chunks_of(d[kk]);
+          my_d += d[kk];
         }
       }
       if (any == 0) continue;  // warp-uniform
+      // distinct nodes of one source: their degrees sum to at most m < 2^32
+      const uint32_t hsum = __reduce_add_sync(kFull, my_h);
+      t_d += __reduce_add_sync(kFull, my_d);
+      t_cnt += mine;
+      uint32_t qb = 0, hb = 0;
+      if (lane == 0) {
+        qb = atomicAdd(&cnt_nx[s], mine);
+        if (hsum) hb = atomicAdd(&hcnt_nx[s], hsum);
+      }
+      uint32_t p = __shfl_sync(kFull, qb, 0);
+      uint32_t hp = __shfl_sync(kFull, hb, 0);
+#pragma unroll 1
+      for (int k4 = 0; k4 < 8; k4 += 4) {
+        // the four words of this half (selects, not indexing, keep the arrays in registers)
+        uint32_t mh[4], dh[4];
+        double ah[4], rs[4];
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        if (m[kk] == 0) continue;
-        if (sl[kk] != slot) {  // flush the counters of the previous source
-          if (lane == 0 && cnt_slot) {
-            atomicAdd(&b.stats[slot].pushes, (unsigned long long)cnt_slot);
-            atomicAdd(&b.stats[slot].edge_pushes, (unsigned long long)dsum);
-            atomicMax(&b.stats[slot].rounds, round);
-            act_next[slot] = 1;
+        for (int kk = 0; kk < 4; ++kk) {
+          mh[kk] = k4 ? m[kk + 4] : m[kk];
+          dh[kk] = k4 ? d[kk + 4] : d[kk];
+          ah[kk] = k4 ? rv[kk + 4] : rv[kk];
+        }
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {  // reserves of four words in flight
+          const uint32_t u = ub + (k4 + kk) * 32 + lane;
+          rs[kk] = ((mh[kk] >> lane) & 1u) ? b.res[g0 + u] : 0.0;
+        }
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t mk = mh[kk];
+          if (mk == 0) continue;  // warp-uniform
+          const bool bit = (mk >> lane) & 1u;
+          const uint32_t dk = dh[kk];
+          const uint32_t nch = bit ? hub_chunks_of(dk) : 0u;
+          const uint32_t nch_incl = hsum ? warp_incl_scan(nch) : 0u;  // lower lanes first
+          if (bit) {
+            const uint32_t u = ub + (k4 + kk) * 32 + lane;
+            const unsigned long long gi = g0 + u;
+            const double a = ah[kk];
+            // the take of round `round`: reserve += alpha a, r = 0, spread increment
+            b.r[gi] = 0.0;
+            b.res[gi] = __dadd_rn(rs[kk], __dmul_rn(alpha, a));
+            const unsigned long long qi = g0 + p + __popc(mk & lt_mask);
+            qn[qi] = ((unsigned long long)s << 32) | u;
+            b.fa[qi] = __ddiv_rn(__dmul_rn(beta, a), (double)dk);
+            const unsigned long long hbase =
+                (unsigned long long)s * b.hub_stride + hp + (nch_incl - nch);
+            for (uint32_t c = 0; c < nch; ++c) hn[hbase + c] = (qi << kHubChunkBits) | c;
           }
-          dsum = 0; cnt_slot = 0;
-          slot = sl[kk];
+          p += __popc(mk);
+          if (hsum) hp += __shfl_sync(kFull, nch_incl, 31);
         }
-        const bool bit = (m[kk] >> lane) & 1u;
-        const uint32_t nch = hub_chunks_of(d[kk]);
-        const uint32_t nch_incl = warp_incl_scan(nch);  // hub items of the lower lanes first
-        if (bit) {
-          const unsigned long long gi = slot * n + u[kk];
-          // the take of round `round`: reserve += alpha a, r = 0, spread increment
-          b.r[gi] = 0.0;
-          b.res[gi] = __dadd_rn(rs[kk], __dmul_rn(alpha, a[kk]));
-          const unsigned long long idx = p + __popc(m[kk] & lt_mask);
-          b.q[nxt][idx] = (slot << 32) | u[kk];
-          b.fa[idx] = __ddiv_rn(__dmul_rn(beta, a[kk]), (double)d[kk]);
-          const unsigned long long hb = hp + (nch_incl - nch);
-          for (uint32_t c = 0; c < nch; ++c) b.hub[nxt][hb + c] = (idx << kHubChunkBits) | c;
-        }
-        p += __popc(m[kk]);
-        hp += __shfl_sync(kFull, nch_incl, 31);
-        dsum += __reduce_add_sync(kFull, d[kk]);
-        cnt_slot += __popc(m[kk]);
       }
     }
-    if (lane == 0 && cnt_slot) {
-      atomicAdd(&b.stats[slot].pushes, (unsigned long long)cnt_slot);
-      atomicAdd(&b.stats[slot].edge_pushes, (unsigned long long)dsum);
-      atomicMax(&b.stats[slot].rounds, round);
-      act_next[slot] = 1;
+    if (lane == 0 && t_cnt) {
+      atomicAdd(&b.stats[s].pushes, (unsigned long long)t_cnt);
+      atomicAdd(&b.stats[s].edge_pushes, t_d);
+      atomicMax(&b.stats[s].rounds, round);
     }
-    pos += nt;
-    hpos += ht;
   }
 }
 
-// End of a round: switch to the new frontier and keep looping while it is non-empty
-// (at most kMaxPushRounds rounds).
-__global__ void k_push_advance(BatchDev b, cudaGraphConditionalHandle loop) {
+// End of a round (one block): the new frontier's per-source group and hub-item prefixes,
+// the list of sources that still push, zeroed counters for the round after, and the
+// loop condition (at most kMaxPushRounds rounds).
+__global__ void __launch_bounds__(1024) k_push_advance(BatchDev b,
+                                                       cudaGraphConditionalHandle loop,
+                                                       int in_graph) {
   PushState* ps = b.ps;
-  ps->cur ^= 1;
-  ps->round += 1;
-  const bool more = b.counters[ps->cur * 2] > 0;
-  const bool go = more && ps->round < kMaxPushRounds;
-  if (more && !go) atomicOr(b.err, kErrPushNotConverged);
-  cudaGraphSetConditional(loop, go ? 1u : 0u);
+  const int cur = ps->cur, nx = cur ^ 1;
+  const int nsrc = b.nsrc;
+  const uint32_t* cnt_nx = b.slot_cnt + (size_t)nx * nsrc;
+  const uint32_t* hcnt_nx = b.slot_cnt + (size_t)(2 + nx) * nsrc;
+  uint32_t* cnt_cur = b.slot_cnt + (size_t)cur * nsrc;
+  uint32_t* hcnt_cur = b.slot_cnt + (size_t)(2 + cur) * nsrc;
+  __shared__ unsigned long long carry_g, carry_h, carry_a;
+  if (threadIdx.x == 0) { carry_g = 0; carry_h = 0; carry_a = 0; }
+  __syncthreads();
+  for (int base = 0; base < nsrc; base += blockDim.x) {
+    const int s = base + (int)threadIdx.x;
+    const uint32_t c = s < nsrc ? cnt_nx[s] : 0u;
+    const uint32_t h = s < nsrc ? hcnt_nx[s] : 0u;
+    unsigned long long ge, he, gt, ht, ae, ze, at, zt;
+    block_scan2((c + 31u) / 32u, h, &ge, &he, &gt, &ht);
+    block_scan2(c > 0 ? 1u : 0u, 0u, &ae, &ze, &at, &zt);
+    if (s < nsrc) {
+      b.gpre[s] = carry_g + ge;
+      b.hpre[s] = carry_h + he;
+      if (c > 0) b.alist[carry_a + ae] = (uint32_t)s;
+      cnt_cur[s] = 0;  // counters of the frontier just spread: they serve the round after
+      hcnt_cur[s] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) { carry_g += gt; carry_h += ht; carry_a += at; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    b.gpre[nsrc] = carry_g;
+    b.hpre[nsrc] = carry_h;
+    ps->ngroups = carry_g;
+    ps->nhub = carry_h;
+    ps->nact = (uint32_t)carry_a;
+    ps->cur = nx;
+    ps->round += 1;
+    b.work[0] = 0;  // dynamic work counters of the next spread
+    b.work[16] = 0;
+    const bool more = carry_a > 0;
+    const bool go = more && ps->round < kMaxPushRounds;
+    if (more && !go) atomicOr(b.err, kErrPushNotConverged);
+    ps->go = go ? 1u : 0u;
+    if (in_graph) cudaGraphSetConditional(loop, go ? 1u : 0u);
+  }
+}
+
+template <typename K>
+int resident_blocks(K kernel, int threads) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess)
+    return 0;
+  return per_sm < 1 ? 1 : per_sm;
 }
 
 }  // namespace
@@ -431,29 +418,20 @@ cudaError_t launch_push_seed(const GraphDev& g, const BatchDev& b, cudaStream_t 
 }
 
 cudaError_t launch_push_body(const GraphDev& g, const BatchDev& b, int num_sms,
-                             cudaGraphConditionalHandle loop, cudaStream_t st) {
-  // one wave of resident blocks: with the dynamic work counter the warps in flight
-  // cover one contiguous window of the sorted frontier
-  static int per_sm = 0;
-  if (per_sm == 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push_spread,
-                                                                  kSpreadThreads, 0);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-  }
-  k_push_spread<<<num_sms * per_sm, kSpreadThreads, 0, st>>>(g, b);
+                             cudaGraphConditionalHandle loop, bool in_graph, cudaStream_t st) {
+  // one wave of resident blocks for the spread (with the dynamic work counter the warps
+  // in flight cover one contiguous window of the frontier) and for the take
+  static int spread_per_sm = 0, take_per_sm = 0;
+  if (spread_per_sm == 0) spread_per_sm = resident_blocks(k_push_spread, kSpreadThreads);
+  if (take_per_sm == 0) take_per_sm = resident_blocks(k_push_take, kTakeThreads);
+  if (spread_per_sm == 0 || take_per_sm == 0) return cudaErrorInvalidConfiguration;
+  k_push_spread<<<num_sms * spread_per_sm, kSpreadThreads, 0, st>>>(g, b);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_push_detect<<<b.residual_grid, kDetectThreads, 0, st>>>(g, b);
+  k_push_take<<<num_sms * take_per_sm, kTakeThreads, 0, st>>>(g, b);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_push_scan<<<1, 1024, 0, st>>>(b);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_push_emit<<<b.residual_grid, kDetectThreads, 0, st>>>(g, b);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_push_advance<<<1, 1, 0, st>>>(b, loop);
+  k_push_advance<<<1, 1024, 0, st>>>(b, loop, in_graph ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -41,10 +41,10 @@ struct Workspace {
   unsigned long long* hub[2] = {nullptr, nullptr};
   double* fa = nullptr;
   unsigned long long* small = nullptr;  // counters[4] totals[2]
-  uint32_t* mask = nullptr;
-  uint32_t* hubw = nullptr;
   unsigned long long* work = nullptr;
-  uint32_t* active = nullptr;
+  uint32_t* alist = nullptr;      // [nsrc] sources with a non-empty frontier
+  uint32_t* slot_cnt = nullptr;   // [4][nsrc] per-source frontier entries and hub items
+  unsigned long long* pre = nullptr;  // [2][nsrc + 1] group and hub-item prefixes
   uint32_t* err = nullptr;
   int32_t* sources = nullptr;
   double* rmax = nullptr;
@@ -63,6 +63,7 @@ struct Workspace {
   uint32_t* h_err = nullptr;
   int32_t* h_sources = nullptr;
   double* h_rmax = nullptr;
+  uint32_t* go_host = nullptr;  // PushState::go of the host-driven push loop
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 
   PushState* ps = nullptr;
@@ -78,7 +79,7 @@ struct Workspace {
     dfree(ps);
     dfree(r); dfree(res); dfree(tally);
     dfree(q[0]); dfree(q[1]); dfree(hub[0]); dfree(hub[1]); dfree(fa);
-    dfree(small); dfree(mask); dfree(hubw); dfree(work); dfree(active); dfree(err); dfree(sources); dfree(rmax); dfree(stats); dfree(blk);
+    dfree(small); dfree(work); dfree(alist); dfree(slot_cnt); dfree(pre); dfree(err); dfree(sources); dfree(rmax); dfree(stats); dfree(blk);
     if (topk_scratch) cudaFree(topk_scratch);
     topk_scratch = nullptr;
     dfree(out_ids); dfree(out_vals); dfree(feat); dfree(pred); dfree(rmax_learned);
@@ -87,7 +88,9 @@ struct Workspace {
     if (h_err) cudaFreeHost(h_err);
     if (h_sources) cudaFreeHost(h_sources);
     if (h_rmax) cudaFreeHost(h_rmax);
+    if (go_host) cudaFreeHost(go_host);
     h_counters = nullptr; h_stats = nullptr; h_err = nullptr; h_sources = nullptr; h_rmax = nullptr;
+    go_host = nullptr;
     cap = 0;
   }
   ~Workspace() {

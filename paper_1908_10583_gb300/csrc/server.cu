@@ -50,7 +50,7 @@ bool compatible(const fora_params& a, const fora_params& b) {
 }
 
 size_t bytes_per_query(const fora_graph* g) {
-  // r, reserve, tally, two frontier queues, increments, mask words, top-k scratch share
+  // r, reserve, tally, two frontier queues, increments, hub items, top-k scratch share
   return (size_t)g->n * 56 + (size_t)g->hub_chunks * 16 + 130 * 1024;
 }
 

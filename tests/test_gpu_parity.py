@@ -320,3 +320,25 @@ def test_autotuner_and_launch_shapes_do_not_change_results(rmat14):
         g.tune("walk_blocks", 7)
     g.tune("spread_width", 1)
     g.tune("walk_blocks", 4)
+
+
+def test_host_driven_push_loop_matches_oracle(rmat14):
+    """push_host_loop=1 launches the same round kernels from the host: same rounds and
+    pushes as the oracle, reserve and residue within the push tolerance."""
+    rp, col, g = rmat14
+    n = len(rp) - 1
+    sources = inputs.uniform_sources(n, 5, 5151)
+    p = fora.Params.make(k=50, seed=9)
+    rmax = g.resolve(p)[0]
+    g.tune("push_host_loop", 1)
+    try:
+        _, _, st, out = run_debug(g, sources, p)
+    finally:
+        g.tune("push_host_loop", 0)
+    for i, s in enumerate(sources):
+        res_o, r_o, pst = oracle.forward_push(rp, col, int(s), 0.2, rmax)
+        np.testing.assert_allclose(out["reserve"][i], res_o, rtol=0, atol=ATOL_PUSH)
+        np.testing.assert_allclose(out["residue"][i], r_o, rtol=0, atol=ATOL_PUSH)
+        assert st[i].pushes == pst.pushes and st[i].push_rounds == pst.rounds
+    with pytest.raises(fora.FORAError):
+        g.tune("push_host_loop", 2)

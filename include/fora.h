@@ -329,6 +329,14 @@ int fora_topk_noalloc(const double *est, int64_t n, int32_t nrows, uint32_t k, i
  * ctr_key (host, [count][6]); writes out (host, [count][4]). */
 int fora_philox_debug(const uint32_t *ctr_key, uint32_t *out, int32_t count);
 
+/* The push's frontier test (Alg. 1: push from v while r(v) > r_max * d_out(v)) as the
+ * device evaluates it, on count host triples: out[i] = 1 iff r[i] > RN64(rmax[i] * d[i]),
+ * for r[i] >= 0, rmax[i] > 0 finite and d[i] >= 1.  The device decides most cases in
+ * FP32 and the rest in FP64; this exposes that test for checking against plain FP64.
+ * All pointers are host memory; returns FORA_ERR_BAD_ARG for count < 0 or null pointers. */
+int fora_threshold_debug(const double *r, const double *rmax, const uint32_t *d, uint8_t *out,
+                         int32_t count);
+
 /*
  * Launch-shape parameters of a graph's queries (results do not depend on them, only
  * speed):  "spread_width" (1..4096, default 1): the push visits the sorted frontier of a

@@ -123,6 +123,8 @@ def load():
         L.fora_topk.argtypes = [P, i64, i32, u32, P, P, P]
         L.fora_philox_debug.restype = I
         L.fora_philox_debug.argtypes = [P, P, i32]
+        L.fora_threshold_debug.restype = I
+        L.fora_threshold_debug.argtypes = [P, P, P, P, i32]
         L.fora_topk_noalloc.restype = I
         L.fora_topk_noalloc.argtypes = [P, i64, i32, u32, P, P, P]
         L.fora_model_create.restype = I
@@ -396,6 +398,17 @@ def philox(ctr_key: np.ndarray) -> np.ndarray:
     out = np.zeros((len(ck), 4), dtype=np.uint32)
     _check(load().fora_philox_debug(ck.ctypes.data, out.ctypes.data, len(ck)))
     return out
+
+
+def threshold(r, rmax, d) -> np.ndarray:
+    """The device's frontier test r > RN(rmax * d) on host arrays -> bool array."""
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    rm = np.ascontiguousarray(np.broadcast_to(rmax, r.shape), dtype=np.float64)
+    dd = np.ascontiguousarray(np.broadcast_to(d, r.shape), dtype=np.uint32)
+    out = np.zeros(r.shape, dtype=np.uint8)
+    _check(load().fora_threshold_debug(r.ctypes.data, rm.ctypes.data, dd.ctypes.data,
+                                       out.ctypes.data, r.size))
+    return out.astype(bool)
 
 
 class Model:

@@ -590,6 +590,27 @@ int fora_philox_debug(const uint32_t* ctr_key, uint32_t* out, int32_t count) {
   return FORA_OK;
 }
 
+int fora_threshold_debug(const double* r, const double* rmax, const uint32_t* d, uint8_t* out,
+                         int32_t count) {
+  if (count < 0 || (count > 0 && (!r || !rmax || !d || !out))) return fail(FORA_ERR_BAD_ARG, "bad arguments");
+  if (count == 0) return FORA_OK;
+  const size_t c = (size_t)count;
+  char* buf = nullptr;  // r [c] | rmax [c] | d [c] | out [c]
+  CUDA_TRY(cudaMalloc(&buf, c * (2 * sizeof(double) + sizeof(uint32_t) + 1)));
+  double* dr = reinterpret_cast<double*>(buf);
+  double* drm = dr + c;
+  uint32_t* dd = reinterpret_cast<uint32_t*>(drm + c);
+  uint8_t* dout = reinterpret_cast<uint8_t*>(dd + c);
+  cudaError_t e = cudaMemcpy(dr, r, c * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(drm, rmax, c * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dd, d, c * sizeof(uint32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_threshold_table(dr, drm, dd, dout, count, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(out, dout, c, cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  CUDA_TRY(e);
+  return FORA_OK;
+}
+
 int fora_graph_tune(fora_graph* g, const char* key, int64_t value) {
   if (!g || !key) return fail(FORA_ERR_BAD_ARG, "null graph or key");
   std::lock_guard<std::mutex> lock(g->mu);

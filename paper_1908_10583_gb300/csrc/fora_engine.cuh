@@ -142,6 +142,9 @@ int report_error(int code, const char* fmt, ...);
 cudaError_t launch_push_seed(const GraphDev& g, const BatchDev& b, cudaStream_t st);
 cudaError_t launch_push_body(const GraphDev& g, const BatchDev& b, int num_sms,
                              cudaGraphConditionalHandle loop, bool in_graph, cudaStream_t st);
+// push.cu: the frontier test r > RN(r_max * d) of the take, on given triples.
+cudaError_t launch_threshold_table(const double* r, const double* rm, const uint32_t* d,
+                                   uint8_t* out, int count, cudaStream_t st);
 
 // walk.cu
 cudaError_t launch_residuals(const GraphDev& g, const BatchDev& b, cudaStream_t st);

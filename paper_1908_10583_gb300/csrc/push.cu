@@ -73,6 +73,30 @@ __device__ __forceinline__ uint32_t hub_chunks_of(uint32_t d) {
   return d > kHubChunk ? (d + kHubChunk - 1) / kHubChunk : 0u;
 }
 
+// r > RN(rm * d), the frontier test, with FP64 arithmetic only near the threshold (this
+// GPU issues about two FP64 operations per clock per SM, so the test itself would bound
+// the scan).  rf is r truncated to 23 mantissa bits through its bit pattern (rf <= r <
+// rf (1 + 2^-23) when r's exponent is in FP32's normal range, rf = 0 when r < 2^-126),
+// tf = RN32(rmf * RN32(d)) with rmf = RN32(rm) is within 2^-22 of V = rm * d, and
+// T = RN64(V) is within 2^-53 of V.  So rf below tf (1 - 2^-19) implies r < V (1 - 2^-20)
+// < T, and rf above tf (1 + 2^-19) implies r > V (1 + 2^-20) > T; in between (and when
+// rmf is outside [2^-100, 2^60], which `fast` excludes) the FP64 test decides.
+__device__ __forceinline__ bool above_threshold(double r, double rm, float rmf, bool fast,
+                                                uint32_t d) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(r);
+  const uint32_t hi = (uint32_t)(bits >> 32);
+  const uint32_t ex = hi >> 20;  // r >= 0: no sign bit
+  if (fast && ex <= 1150u) {
+    const float tf = rmf * __uint2float_rn(d);
+    const float rf = ex < 897u ? 0.0f
+                               : __uint_as_float(((ex - 896u) << 23) | ((hi & 0xFFFFFu) << 3) |
+                                                 ((uint32_t)bits >> 29));
+    if (rf < tf * (1.0f - 0x1p-19f)) return false;
+    if (rf > tf * (1.0f + 0x1p-19f)) return true;
+  }
+  return r > __dmul_rn(rm, (double)d);
+}
+
 // The source whose range [pre[s], pre[s + 1]) holds x, for a non-decreasing prefix with
 // x < pre[nsrc]: the largest s with pre[s] <= x (empty sources have pre[s] = pre[s + 1]).
 __device__ __forceinline__ int slot_of(const unsigned long long* pre, int nsrc,
@@ -250,6 +274,8 @@ __global__ void __launch_bounds__(kTakeThreads, 3) k_push_take(GraphDev g, Batch
     const uint32_t s = b.alist[t / tps];
     const uint32_t tb = (uint32_t)((t % tps) * kTileNodes);
     const double rm = b.rmax[s];
+    const float rmf = __double2float_rn(rm);
+    const bool fast = rmf >= 0x1p-100f && rmf <= 0x1p60f;
     const unsigned long long g0 = (unsigned long long)s * n;
     uint32_t t_cnt = 0;
     unsigned long long t_d = 0;
@@ -277,7 +303,7 @@ __global__ void __launch_bounds__(kTakeThreads, 3) k_push_take(GraphDev g, Batch
       }
 #pragma unroll
       for (int kk = 0; kk < 8; ++kk) {
-        const bool cross = rv[kk] > __dmul_rn(rm, (double)d[kk]);
+        const bool cross = above_threshold(rv[kk], rm, rmf, fast, d[kk]);
         m[kk] = __ballot_sync(kFull, cross);
         any |= m[kk];
         mine += __popc(m[kk]);
@@ -401,6 +427,16 @@ __global__ void __launch_bounds__(1024) k_push_advance(BatchDev b,
   }
 }
 
+// The frontier test of k_push_take on given (r, r_max, d) triples.
+__global__ void k_threshold_table(const double* r, const double* rm, const uint32_t* d,
+                                  uint8_t* out, int count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const float rmf = __double2float_rn(rm[i]);
+  const bool fast = rmf >= 0x1p-100f && rmf <= 0x1p60f;
+  out[i] = above_threshold(r[i], rm[i], rmf, fast, d[i]) ? 1 : 0;
+}
+
 template <typename K>
 int resident_blocks(K kernel, int threads) {
   int per_sm = 0;
@@ -410,6 +446,13 @@ int resident_blocks(K kernel, int threads) {
 }
 
 }  // namespace
+
+cudaError_t launch_threshold_table(const double* r, const double* rm, const uint32_t* d,
+                                   uint8_t* out, int count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  k_threshold_table<<<(count + 255) / 256, 256, 0, st>>>(r, rm, d, out, count);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_push_seed(const GraphDev& g, const BatchDev& b, cudaStream_t st) {
   const int threads = 256;

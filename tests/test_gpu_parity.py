@@ -342,3 +342,40 @@ def test_host_driven_push_loop_matches_oracle(rmat14):
         assert st[i].pushes == pst.pushes and st[i].push_rounds == pst.rounds
     with pytest.raises(fora.FORAError):
         g.tune("push_host_loop", 2)
+
+
+def test_device_frontier_test_equals_fp64_comparison():
+    """The take decides r > RN(r_max * d) mostly in FP32 from the bit pattern of r; on
+    values at, next to and around the threshold (within 2^-22 ... 2^-17 of it, where the
+    FP32 band ends), at zero, denormal and FP32-underflow residues, and for r_max outside
+    the FP32 fast range, the result must equal the plain FP64 comparison."""
+    rng = np.random.default_rng(77)
+    rmaxes = [1.9e-8, 0.1234, 3e-30, 1e-200, 2.0 ** -100, 2.0 ** -99, 1e20, 0.75, 4.2e-13]
+    degs = [1, 2, 3, 16, 255, 256, 257, 1000, 2 ** 23 + 1, 2 ** 24 + 3, 2 ** 31 + 5]
+    R, RM, D = [], [], []
+    for rm in rmaxes:
+        for d in degs:
+            T = rm * float(d)
+            cand = [T, 0.0, 5e-324, 2.0 ** -126, 2.0 ** -127, np.nextafter(2.0 ** -126, 0), 1.0,
+                    2.0 * T, 0.5 * T]
+            x = T
+            for _ in range(3):
+                x = np.nextafter(x, np.inf)
+                cand.append(x)
+            x = T
+            for _ in range(3):
+                x = np.nextafter(x, 0.0)
+                cand.append(x)
+            for e in (17, 18, 19, 20, 21, 22, 23, 24):
+                cand += [T * (1 + 2.0 ** -e), T * (1 - 2.0 ** -e)]
+            cand += list(T * (1 + rng.uniform(-2.0 ** -17, 2.0 ** -17, 200)))
+            cand = [c for c in cand if np.isfinite(c) and c >= 0]
+            R += cand
+            RM += [rm] * len(cand)
+            D += [d] * len(cand)
+    R, RM, D = np.array(R), np.array(RM), np.array(D, dtype=np.uint32)
+    want = R > RM * D.astype(np.float64)
+    got = fora.threshold(R, RM, D)
+    bad = np.flatnonzero(got != want)
+    assert bad.size == 0, [(R[i], RM[i], D[i], got[i]) for i in bad[:5]]
+    assert want.any() and (~want).any()

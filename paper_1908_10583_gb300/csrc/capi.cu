@@ -241,6 +241,7 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
   b.alpha_threshold = rp.alpha_threshold;
   b.seed = p->seed;
   b.zero_hop = (p->flags & FORA_ZERO_HOP) != 0;
+  b.want_count = dbg && dbg->count;
   b.r = w->r; b.res = w->res; b.tally = w->tally;
   b.q[0] = w->q[0]; b.q[1] = w->q[1]; b.fa = w->fa;
   b.hub[0] = w->hub[0]; b.hub[1] = w->hub[1];

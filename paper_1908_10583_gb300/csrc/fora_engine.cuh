@@ -94,6 +94,7 @@ struct BatchDev {
   uint32_t alpha_threshold;  // floor(alpha * 2^32)
   uint64_t seed;
   int zero_hop;              // walk phase with zero-hop pruning (Section 4.1)
+  int want_count;            // tally walk counts too (only a debug output reads them)
   double* r;                 // residue, later the estimate
   double* res;               // reserve
   Tally* tally;              // walk ends per (source, node)

@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(kWalkThreads, kMinBlocks) k_walks(GraphDev g, 
       if (!forced && rng.next() < t_alpha) {
         // the walk stops at x (Section 2.1): count it and add its weight (Alg. 2)
         Tally* t = b.tally + (unsigned long long)slot * (unsigned long long)g.n + x;
-        atomicAdd(&t->cnt, 1u);
+        if (b.want_count) atomicAdd(&t->cnt, 1u);
         atomicAdd(&t->acc, wgt);
         if (slot != cur_slot) {
           if (steps_here) atomicAdd(&b.stats[cur_slot].walk_steps, steps_here);

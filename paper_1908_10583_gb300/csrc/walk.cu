@@ -233,8 +233,10 @@ __device__ __forceinline__ unsigned long long warp_find_entry(const unsigned lon
 // goes to warp c mod (number of warps), so the walks in flight at any time are a
 // narrow window of the source-major walk space and their end tallies stay in L2.
 // Per chunk the warp first maps every walk to its residual entry (into shared
-// memory, relative to the chunk's first entry), then each lane runs its 32 walks
-// as an independent state machine (one move or one walk end per loop iteration).
+// memory, relative to the chunk's first entry), then each lane runs walks as a state
+// machine (one move or one walk end per loop iteration), taking the chunk's next
+// unstarted walk whenever its walk ends: walk lengths are geometric, and with a fixed
+// share of walks per lane the warp would wait for its longest share.
 template <int kMinBlocks>
 __global__ void __launch_bounds__(kWalkThreads, kMinBlocks) k_walks(GraphDev g, BatchDev b) {
   __shared__ uint16_t smap[kWalkWarps][kChunk];
@@ -273,6 +275,9 @@ __global__ void __launch_bounds__(kWalkThreads, kMinBlocks) k_walks(GraphDev g, 
     }
     __syncwarp();
 
+    // walks are handed to lanes in order as lanes finish (a warp-uniform counter), so
+    // no lane idles while the chunk has unstarted walks
+    uint32_t next_walk = 32;  // warp-uniform
     uint32_t i = lane;
     bool have = i < cnt;
     WalkStream rng;
@@ -290,8 +295,12 @@ __global__ void __launch_bounds__(kWalkThreads, kMinBlocks) k_walks(GraphDev g, 
       wgt = b.wr_weight[idx];
       steps = 0;
     }
-    while (have) {
-      if (!forced && rng.next() < t_alpha) {
+    for (;;) {
+      // one step of every lane: a stop test, then either a walk end or a move
+      bool stop = false;
+      if (have && !forced) stop = rng.next() < t_alpha;
+      const uint32_t stops = __ballot_sync(kFull, stop);
+      if (stop) {
         // the walk stops at x (Section 2.1): count it and add its weight (Alg. 2)
         Tally* t = b.tally + (unsigned long long)slot * (unsigned long long)g.n + x;
         if (b.want_count) atomicAdd(&t->cnt, 1u);
@@ -302,7 +311,7 @@ __global__ void __launch_bounds__(kWalkThreads, kMinBlocks) k_walks(GraphDev g, 
           cur_slot = slot;
         }
         steps_here += steps;
-        i += 32;
+        i = next_walk + (uint32_t)__popc(stops & ((1u << lane) - 1u));
         have = i < cnt;
         if (have) {
           const unsigned long long idx = idx0 + smap[wid][i];
@@ -314,26 +323,36 @@ __global__ void __launch_bounds__(kWalkThreads, kMinBlocks) k_walks(GraphDev g, 
           steps = 0;
           forced = b.zero_hop;
         }
-        continue;
-      }
-      forced = false;
-      if (steps >= kMaxSteps) { capped = true; have = false; break; }
-      const uint32_t rb0 = g.row[x];
-      const uint32_t d = g.row[x + 1] - rb0;
-      unsigned long long m = (unsigned long long)rng.next() * d;
-      uint32_t low = (uint32_t)m;
-      if (low < d) {
-        const uint32_t reject_below = (0u - d) % d;
-        // each retry happens with probability < d / 2^32; 64 in a row never occur in practice
-        for (int tries = 0; low < reject_below && tries < 64; ++tries) {
-          m = (unsigned long long)rng.next() * d;
-          low = (uint32_t)m;
+      } else if (have) {
+        forced = false;
+        if (steps >= kMaxSteps) {
+          capped = true;
+          have = false;
+        } else {
+          const uint32_t rb0 = g.row[x];
+          const uint32_t d = g.row[x + 1] - rb0;
+          unsigned long long m = (unsigned long long)rng.next() * d;
+          uint32_t low = (uint32_t)m;
+          if (low < d) {
+            const uint32_t reject_below = (0u - d) % d;
+            // each retry happens with probability < d / 2^32; 64 in a row never occur
+            for (int tries = 0; low < reject_below && tries < 64; ++tries) {
+              m = (unsigned long long)rng.next() * d;
+              low = (uint32_t)m;
+            }
+          }
+          if (low < d && low < (0u - d) % d) {
+            capped = true;
+            have = false;
+          } else {
+            const uint32_t e = rb0 + (uint32_t)(m >> 32);
+            x = g.colbits ? packed_target(g.colp, g.colbits, e) : (uint32_t)g.col[e];
+            ++steps;
+          }
         }
-        if (low < reject_below) { capped = true; have = false; break; }
       }
-      const uint32_t e = rb0 + (uint32_t)(m >> 32);
-      x = g.colbits ? packed_target(g.colp, g.colbits, e) : (uint32_t)g.col[e];
-      ++steps;
+      next_walk += (uint32_t)__popc(stops);
+      if (!__any_sync(kFull, have)) break;
     }
     __syncwarp();
   }

@@ -279,8 +279,8 @@ def run_fora(args):
     def collect(step, st, ms):
         rounds = max(s.push_rounds for s in st)
         # push: the seed, then (rounds + 1) passes of the loop body (spread, take,
-        # advance); residuals 3, walks 1, estimate 1, top-k select 19
-        counters["launches"] += 1 + 3 * (rounds + 1) + 3 + 1 + 1 + 19
+        # advance); residuals 4, walks 1, estimate 1, top-k select 19
+        counters["launches"] += 1 + 3 * (rounds + 1) + 4 + 1 + 1 + 19
         if model is not None:
             counters["launches"] += 3  # features, forward, r_max
         for key in phase:

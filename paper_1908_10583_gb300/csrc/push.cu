@@ -79,22 +79,32 @@ __device__ __forceinline__ uint32_t hub_chunks_of(uint32_t d) {
 // rf (1 + 2^-23) when r's exponent is in FP32's normal range, rf = 0 when r < 2^-126),
 // tf = RN32(rmf * RN32(d)) with rmf = RN32(rm) is within 2^-22 of V = rm * d, and
 // T = RN64(V) is within 2^-53 of V.  So rf below tf (1 - 2^-19) implies r < V (1 - 2^-20)
-// < T, and rf above tf (1 + 2^-19) implies r > V (1 + 2^-20) > T; in between (and when
-// rmf is outside [2^-100, 2^60], which `fast` excludes) the FP64 test decides.
-__device__ __forceinline__ bool above_threshold(double r, double rm, float rmf, bool fast,
-                                                uint32_t d) {
+// < T, and rf above tf (1 + 2^-19) implies r > V (1 + 2^-20) > T.  Returns 0 (below),
+// 1 (above) or 2 (undecided: in between, or rmf outside [2^-100, 2^60], which `fast`
+// excludes, or r >= 2^128); the FP64 test decides the undecided ones.
+__device__ __forceinline__ uint32_t threshold_fast(double r, float rmf, bool fast, uint32_t d) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(r);
   const uint32_t hi = (uint32_t)(bits >> 32);
   const uint32_t ex = hi >> 20;  // r >= 0: no sign bit
-  if (fast && ex <= 1150u) {
-    const float tf = rmf * __uint2float_rn(d);
-    const float rf = ex < 897u ? 0.0f
-                               : __uint_as_float(((ex - 896u) << 23) | ((hi & 0xFFFFFu) << 3) |
-                                                 ((uint32_t)bits >> 29));
-    if (rf < tf * (1.0f - 0x1p-19f)) return false;
-    if (rf > tf * (1.0f + 0x1p-19f)) return true;
-  }
+  if (!fast || ex > 1150u) return 2u;
+  const float tf = rmf * __uint2float_rn(d);
+  const float rf = ex < 897u ? 0.0f
+                             : __uint_as_float(((ex - 896u) << 23) | ((hi & 0xFFFFFu) << 3) |
+                                               ((uint32_t)bits >> 29));
+  if (rf < tf * (1.0f - 0x1p-19f)) return 0u;
+  if (rf > tf * (1.0f + 0x1p-19f)) return 1u;
+  return 2u;
+}
+
+// The FP64 test, kept out of line so that it is not evaluated for every node.
+__device__ __noinline__ bool threshold_exact(double r, double rm, uint32_t d) {
   return r > __dmul_rn(rm, (double)d);
+}
+
+__device__ __forceinline__ bool above_threshold(double r, double rm, float rmf, bool fast,
+                                                uint32_t d) {
+  const uint32_t f = threshold_fast(r, rmf, fast, d);
+  return f == 2u ? threshold_exact(r, rm, d) : f == 1u;
 }
 
 // The source whose range [pre[s], pre[s + 1]) holds x, for a non-decreasing prefix with
@@ -270,6 +280,11 @@ __global__ void __launch_bounds__(kTakeThreads, 3) k_push_take(GraphDev g, Batch
   const uint32_t lt_mask = (1u << lane) - 1u;
   const unsigned long long wpb = blockDim.x >> 5;
   const unsigned long long nwarps = (unsigned long long)gridDim.x * wpb;
+  __shared__ uint32_t stage_u[kTakeThreads / 32][256], stage_d[kTakeThreads / 32][256];
+  __shared__ double stage_a[kTakeThreads / 32][256];
+  uint32_t* st_u = stage_u[threadIdx.x >> 5];
+  uint32_t* st_d = stage_d[threadIdx.x >> 5];
+  double* st_a = stage_a[threadIdx.x >> 5];
   for (unsigned long long t = blockIdx.x * wpb + (threadIdx.x >> 5); t < ntiles; t += nwarps) {
     const uint32_t s = b.alist[t / tps];
     const uint32_t tb = (uint32_t)((t % tps) * kTileNodes);
@@ -301,9 +316,20 @@ __global__ void __launch_bounds__(kTakeThreads, 3) k_push_take(GraphDev g, Batch
         const uint32_t down = __shfl_down_sync(kFull, d[kk], 1);
         d[kk] = (lane < 31 ? down : first_next) - d[kk];
       }
+      uint32_t above = 0, undecided = 0;  // bit kk: word kk of this lane
 #pragma unroll
       for (int kk = 0; kk < 8; ++kk) {
-        const bool cross = above_threshold(rv[kk], rm, rmf, fast, d[kk]);
+        const uint32_t f = threshold_fast(rv[kk], rmf, fast, d[kk]);
+        above |= (f == 1u ? 1u : 0u) << kk;
+        undecided |= (f == 2u ? 1u : 0u) << kk;
+      }
+      if (__any_sync(kFull, undecided != 0)) {  // rare: a residue within 2^-19 of its threshold
+        for (int kk = 0; kk < 8; ++kk)
+          if (((undecided >> kk) & 1u) && threshold_exact(rv[kk], rm, d[kk])) above |= 1u << kk;
+      }
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {
+        const bool cross = (above >> kk) & 1u;
         m[kk] = __ballot_sync(kFull, cross);
         any |= m[kk];
         mine += __popc(m[kk]);
@@ -322,50 +348,53 @@ __global__ void __launch_bounds__(kTakeThreads, 3) k_push_take(GraphDev g, Batch
         qb = atomicAdd(&cnt_nx[s], mine);
         if (hsum) hb = atomicAdd(&hcnt_nx[s], hsum);
       }
-      uint32_t p = __shfl_sync(kFull, qb, 0);
-      uint32_t hp = __shfl_sync(kFull, hb, 0);
-#pragma unroll 1
-      for (int k4 = 0; k4 < 8; k4 += 4) {
-        // the four words of this half (selects, not indexing, keep the arrays in registers)
-        uint32_t mh[4], dh[4];
-        double ah[4], rs[4];
+      qb = __shfl_sync(kFull, qb, 0);
+      hb = __shfl_sync(kFull, hb, 0);
+      // the batch's crossing nodes, packed in (word, lane) order into this warp's stage,
+      // so the take's FP64 arithmetic runs on 32 crossing nodes per instruction
+      {
+        uint32_t before = 0;
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          mh[kk] = k4 ? m[kk + 4] : m[kk];
-          dh[kk] = k4 ? d[kk + 4] : d[kk];
-          ah[kk] = k4 ? rv[kk + 4] : rv[kk];
-        }
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {  // reserves of four words in flight
-          const uint32_t u = ub + (k4 + kk) * 32 + lane;
-          rs[kk] = ((mh[kk] >> lane) & 1u) ? b.res[g0 + u] : 0.0;
-        }
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const uint32_t mk = mh[kk];
-          if (mk == 0) continue;  // warp-uniform
-          const bool bit = (mk >> lane) & 1u;
-          const uint32_t dk = dh[kk];
-          const uint32_t nch = bit ? hub_chunks_of(dk) : 0u;
-          const uint32_t nch_incl = hsum ? warp_incl_scan(nch) : 0u;  // lower lanes first
-          if (bit) {
-            const uint32_t u = ub + (k4 + kk) * 32 + lane;
-            const unsigned long long gi = g0 + u;
-            const double a = ah[kk];
-            // the take of round `round`: reserve += alpha a, r = 0, spread increment
-            b.r[gi] = 0.0;
-            b.res[gi] = __dadd_rn(rs[kk], __dmul_rn(alpha, a));
-            const unsigned long long qi = g0 + p + __popc(mk & lt_mask);
-            qn[qi] = ((unsigned long long)s << 32) | u;
-            b.fa[qi] = __ddiv_rn(__dmul_rn(beta, a), (double)dk);
-            const unsigned long long hbase =
-                (unsigned long long)s * b.hub_stride + hp + (nch_incl - nch);
-            for (uint32_t c = 0; c < nch; ++c) hn[hbase + c] = (qi << kHubChunkBits) | c;
+        for (int kk = 0; kk < 8; ++kk) {
+          if ((m[kk] >> lane) & 1u) {
+            const uint32_t e = before + __popc(m[kk] & lt_mask);
+            st_u[e] = ub + kk * 32 + lane;
+            st_d[e] = d[kk];
+            st_a[e] = rv[kk];
           }
-          p += __popc(mk);
-          if (hsum) hp += __shfl_sync(kFull, nch_incl, 31);
+          before += __popc(m[kk]);
         }
       }
+      __syncwarp();
+      uint32_t hp = hb;
+      for (uint32_t e0 = 0; e0 < mine; e0 += 32) {
+        const uint32_t e = e0 + lane;
+        const bool live = e < mine;
+        uint32_t u = 0, dk = 1;
+        double a = 0.0, rs = 0.0;
+        if (live) {
+          u = st_u[e];
+          dk = st_d[e];
+          a = st_a[e];
+          rs = b.res[g0 + u];
+        }
+        const uint32_t nch = live ? hub_chunks_of(dk) : 0u;
+        const uint32_t nch_incl = hsum ? warp_incl_scan(nch) : 0u;  // lower entries first
+        if (live) {
+          const unsigned long long gi = g0 + u;
+          // the take of round `round`: reserve += alpha a, r = 0, spread increment
+          b.r[gi] = 0.0;
+          b.res[gi] = __dadd_rn(rs, __dmul_rn(alpha, a));
+          const unsigned long long qi = g0 + qb + e;
+          qn[qi] = ((unsigned long long)s << 32) | u;
+          b.fa[qi] = __ddiv_rn(__dmul_rn(beta, a), (double)dk);
+          const unsigned long long hbase =
+              (unsigned long long)s * b.hub_stride + hp + (nch_incl - nch);
+          for (uint32_t c = 0; c < nch; ++c) hn[hbase + c] = (qi << kHubChunkBits) | c;
+        }
+        if (hsum) hp += __shfl_sync(kFull, nch_incl, 31);
+      }
+      __syncwarp();
     }
     if (lane == 0 && t_cnt) {
       atomicAdd(&b.stats[s].pushes, (unsigned long long)t_cnt);

@@ -55,10 +55,48 @@ struct WalkStream {
   }
 };
 
-// omega_v = ceil(r * C); W_v = rint((r / omega_v) * 2^63)
-__device__ __forceinline__ double walks_of(double r, double C) { return ceil(__dmul_rn(r, C)); }
+// omega_v = ceil(RN64(r * C)); W_v = rint((r / omega_v) * 2^63)
+__device__ __noinline__ unsigned long long walks_exact(double r, double C) {
+  return (unsigned long long)ceil(__dmul_rn(r, C));
+}
 __device__ __forceinline__ unsigned long long weight_of(double r, double omega) {
   return __double2ull_rn(__dmul_rn(__ddiv_rn(r, omega), 0x1p63));
+}
+
+constexpr uint32_t kOmegaUndecided = 0xFFFFFFFFu;
+
+// omega_v for r > 0 without FP64 arithmetic where FP32 decides it (this GPU issues about
+// two FP64 operations per clock per SM).  rf = r truncated to 23 mantissa bits (rf <= r
+// < rf (1 + 2^-23)) and cf = RN32(C) give P = RN32(rf * cf) within 2^-22 of V = r * C,
+// and T = RN64(V) is within 2^-53 of V; so T lies strictly inside (P (1 - 2^-20),
+// P (1 + 2^-20)), and when that band holds no integer, ceil(T) = floor(band) + 1.
+// Returns kOmegaUndecided otherwise (an integer in the band, P >= 2^22, r outside FP32's
+// normal range, or C outside [1, 2^100], which `fast` excludes).
+__device__ __forceinline__ uint32_t walks_fast(double r, float cf, bool fast) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(r);
+  const uint32_t hi = (uint32_t)(bits >> 32);
+  const uint32_t ex = hi >> 20;  // r > 0: no sign bit
+  if (!fast || ex < 897u || ex > 1150u) return kOmegaUndecided;
+  const float rf =
+      __uint_as_float(((ex - 896u) << 23) | ((hi & 0xFFFFFu) << 3) | ((uint32_t)bits >> 29));
+  const float pr = rf * cf;
+  if (!(pr < 0x1p22f)) return kOmegaUndecided;
+  const float lo = pr * (1.0f - 0x1p-20f), up = pr * (1.0f + 0x1p-20f);
+  const float fl = floorf(lo);
+  if (floorf(up) != fl || fl == lo) return kOmegaUndecided;
+  return (uint32_t)fl + 1u;
+}
+
+// omega_v of this lane's residue (0 when r = 0); every lane of the warp must call it.
+__device__ __forceinline__ unsigned long long walks_of(double r, double C, float cf, bool fast) {
+  const bool live = __double_as_longlong(r) != 0;  // residues are >= 0, never -0
+  const uint32_t f = live ? walks_fast(r, cf, fast) : 0u;
+  unsigned long long w = f;
+  const bool undecided = f == kOmegaUndecided;
+  if (__any_sync(kFull, undecided)) {  // rare: r * C within 2^-20 of an integer
+    if (undecided) w = walks_exact(r, C);
+  }
+  return w;
 }
 
 // The residue the walks sample: r, or (1 - alpha) r with zero-hop pruning (Section 4.1).
@@ -119,8 +157,11 @@ __global__ void __launch_bounds__(kResidualThreads) k_residual_count(GraphDev g,
   unsigned long long slot_end = (unsigned long long)(slot + 1) * (unsigned long long)g.n;
   unsigned long long s_cnt = 0, s_walks = 0;
   double s_sum = 0.0;
-  for (; i < end; i += kResidualThreads) {
-    while (i >= slot_end) {
+  const float cf = __double2float_rn(b.walk_scale);
+  const bool fast = cf >= 1.0f && cf <= 0x1p100f;
+  for (unsigned long long base = beg; base < end; base += kResidualThreads, i += kResidualThreads) {
+    const bool valid = i < end;
+    while (valid && i >= slot_end) {
       if (s_cnt) {
         atomicAdd(&b.stats[slot].residual_nodes, s_cnt);
         atomicAdd(&b.stats[slot].walks, s_walks);
@@ -130,10 +171,10 @@ __global__ void __launch_bounds__(kResidualThreads) k_residual_count(GraphDev g,
       ++slot;
       slot_end += (unsigned long long)g.n;
     }
-    const double r = b.r[i];
-    if (r > 0.0) {
-      // an entry of R needs at least one walk (omega_v = 0 only if r * C underflows)
-      const unsigned long long w = (unsigned long long)walks_of(sampled(b, r), b.walk_scale);
+    const double r = valid ? b.r[i] : 0.0;
+    // an entry of R needs at least one walk (omega_v = 0 only if r * C underflows)
+    const unsigned long long w = walks_of(sampled(b, r), b.walk_scale, cf, fast);
+    if (__double_as_longlong(r) != 0) {
       if (w > 0) { ++cnt; walks += w; }
       ++s_cnt; s_walks += w; s_sum += r;
     }
@@ -185,22 +226,38 @@ __global__ void __launch_bounds__(kResidualThreads) k_residual_emit(GraphDev g, 
   block_range(total, blockIdx.x, gridDim.x, &beg, &end);
   unsigned long long pos = b.blk_cnt[blockIdx.x];
   unsigned long long woff = b.blk_walks[blockIdx.x];
+  const float cf = __double2float_rn(b.walk_scale);
+  const bool fast = cf >= 1.0f && cf <= 0x1p100f;
   for (unsigned long long tile = beg; tile < end; tile += kResidualThreads) {
     const unsigned long long i = tile + threadIdx.x;
     const double r = i < end ? sampled(b, b.r[i]) : 0.0;
-    const double omega = r > 0.0 ? walks_of(r, b.walk_scale) : 0.0;
-    const bool live = omega >= 1.0;
+    const unsigned long long omega = walks_of(r, b.walk_scale, cf, fast);
+    const bool live = omega >= 1;
     unsigned long long ce, we, ct, wt;
-    block_excl_scan2(live ? 1ull : 0ull, (unsigned long long)omega, &ce, &we, &ct, &wt);
+    block_excl_scan2(live ? 1ull : 0ull, omega, &ce, &we, &ct, &wt);
     if (live) {
       const unsigned long long slot = i / (unsigned long long)g.n;
       const unsigned long long v = i - slot * (unsigned long long)g.n;
       b.wr_entry[pos + ce] = (slot << 32) | v;
       b.wr_offset[pos + ce] = woff + we;
-      b.wr_weight[pos + ce] = weight_of(r, omega);
+      // the residue for now; k_residual_weight turns it into the walk weight
+      b.wr_weight[pos + ce] = (unsigned long long)__double_as_longlong(r);
     }
     pos += ct;
     woff += wt;
+  }
+}
+
+// W_v of every entry of R, densely over the list (omega_v = offset[i + 1] - offset[i]),
+// so the FP64 division runs on 32 entries per instruction.
+__global__ void __launch_bounds__(kResidualThreads) k_residual_weight(BatchDev b) {
+  const unsigned long long nR = b.totals[0];
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < nR;
+       i += stride) {
+    const double r = __longlong_as_double((long long)b.wr_weight[i]);
+    const double omega = (double)(b.wr_offset[i + 1] - b.wr_offset[i]);
+    b.wr_weight[i] = weight_of(r, omega);
   }
 }
 
@@ -389,6 +446,9 @@ cudaError_t launch_residuals(const GraphDev& g, const BatchDev& b, cudaStream_t 
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_residual_emit<<<b.residual_grid, kResidualThreads, 0, st>>>(g, b);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_residual_weight<<<b.residual_grid, kResidualThreads, 0, st>>>(b);
   return cudaGetLastError();
 }
 

@@ -31,9 +31,11 @@ UNIT = "queries/s"
 WALK_BYTES_PER_MOVE = 12      # row_ptr pair (8 B) + col entry (4 B)
 WALK_BYTES_PER_WALK = 24      # count RMW (4+4 B) + acc RMW (8+8 B)
 WALK_BYTES_PER_ENTRY = 24     # residual entry, offset, weight (8 B each)
+PUSH_BYTES_PER_EDGE = 20      # col entry (4 B) + FP64 read-modify-write of r(u) (16 B)
+PUSH_BYTES_PER_VERTEX = 44    # row pair, r(v) read and zero, reserve RMW, queue append
 
 
-def parse_args():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -56,7 +58,7 @@ def parse_args():
                     help="skip fora_graph_autotune (launch shapes at their defaults / --tune)")
     ap.add_argument("--plain-sources", type=int, default=16,
                     help="single-source queries timed for the plain-FORA comparison")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def workload(args):
@@ -161,6 +163,28 @@ def dist_setup():
     return world, rank, local
 
 
+def replica_sources(n, count, rank, step):
+    """Sources of one step on one replica: a seeded uniform draw per (rank, step), so the
+    replicas of an N-GPU run work on disjoint streams of new queries."""
+    import inputs
+    return inputs.uniform_sources(n, count, inputs.SOURCE_SEED + 1_000_003 * rank + 7919 * step)
+
+
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest value of x over the ranks of the process group (x itself at N = 1)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units all ranks processed per second, with `seconds` the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 def run_reference(args):
     """CPU oracle arm: each step is a bounded sample of the workload on the host cores."""
     world, rank, _ = dist_setup()
@@ -237,7 +261,7 @@ def run_fora(args):
     model = fora.Model.load_file(model_path) if mode == "learned" else None
 
     def sources(step):
-        return inputs.uniform_sources(n, B, inputs.SOURCE_SEED + 1_000_003 * rank + 7919 * step)
+        return replica_sources(n, B, rank, step)
 
     def one_step(src, use_model):
         if use_model is not None:
@@ -273,6 +297,7 @@ def run_fora(args):
     clocks = ClockSampler(local)
     clocks.start()
     walk_ms, walk_bytes = [], []
+    push_ms, push_bytes = [], []
     phase = {"ms_push": 0.0, "ms_residual": 0.0, "ms_walk": 0.0, "ms_topk": 0.0}
     counters = {"launches": 0, "walks": 0, "moves": 0}
 
@@ -286,6 +311,9 @@ def run_fora(args):
         for key in phase:
             phase[key] += getattr(st[0], key)
         walk_ms.append(st[0].ms_walk)
+        push_ms.append(st[0].ms_push)
+        push_bytes.append(PUSH_BYTES_PER_EDGE * sum(s.edge_pushes for s in st) +
+                          PUSH_BYTES_PER_VERTEX * sum(s.pushes for s in st))
         nw = sum(s.walks for s in st)
         ns = sum(s.walk_steps for s in st)
         nr = sum(s.residual_nodes for s in st)
@@ -304,12 +332,8 @@ def run_fora(args):
     step_ms = timed(model, args.steps, collect)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = B * args.steps * world / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
+    value = whole_job_rate(B * args.steps, world, total_ms / 1e3)
     launches = counters["launches"]
     walks_total, steps_total = counters["walks"], counters["moves"]
 
@@ -341,7 +365,8 @@ def run_fora(args):
         else:
             g.ssppr_batch_host(src, params, h_ids, h_vals, stream=stream)
         e2e_s += time.perf_counter() - t0
-    e2e = {"value": B * args.steps / e2e_s, "unit": UNIT,
+    e2e_s = max_over_ranks(e2e_s, dist, "cuda")
+    e2e = {"value": whole_job_rate(B * args.steps, world, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": B * (4 + 8),
            "d2h_bytes_per_step": B * k * (4 + 8)}
 
@@ -351,6 +376,12 @@ def run_fora(args):
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": profiled_traffic("k_walks", args.workload),
                 "algorithmic_bytes_per_launch": sum(walk_bytes) / len(walk_bytes)}
+    # the push phase (all its rounds: spread, take, advance) against the same peak
+    achieved_push = (sum(push_bytes) / len(push_bytes)) / (statistics.mean(push_ms) / 1e3) / 1e9
+    roofline_push = {"bound": "hbm", "kernels": "k_push_spread+k_push_take+k_push_advance",
+                     "achieved": achieved_push, "peak": peak, "peak_kind": peak_kind,
+                     "unit": "GB/s", "frac": achieved_push / peak, "traffic": None,
+                     "algorithmic_bytes_per_step": sum(push_bytes) / len(push_bytes)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -381,6 +412,7 @@ def run_fora(args):
             "gpu_launches": launches,
             "comparison": comparison,
             "roofline": roofline,
+            "roofline_push": roofline_push,
             "e2e": e2e,
             "clocks": clk}
     if cpu is not None:

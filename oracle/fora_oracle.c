@@ -13,8 +13,8 @@
  *     (Alg. 2) and the r_max rule (Eq. rmax, Section 3.2, with its
  *     Case 2 fallback when m * r_max > 1);
  *   - Forward Push (Alg. 1), run as synchronous rounds: round t takes the set
- *     F_t of every v with r(v)/d_out(v) > r_max (the reading "identifies every
- *     node v with ..." of Section 2.2), first moves alpha*r(v) to the reserve
+ *     F_t of every v with r(v)/d_out(v) > r_max (Section 2.2 takes all nodes
+ *     above the threshold at once), first moves alpha*r(v) to the reserve
  *     and zeroes r(v) for all of F_t, then spreads (1-alpha)*r(v)/d_out(v) to
  *     every out-neighbour; residue arriving at a node of F_t during round t
  *     waits for round t+1.  The test is written r(v) > r_max * d_out(v);

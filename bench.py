@@ -132,17 +132,21 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def profiled_traffic(kernel, wl):
+def profiled_traffic(kernel, wl, launches_per_step=1):
     """DRAM bytes per launch from a committed ncu summary (profiles/<kernel>_<wl>.txt,
-    line 'dram_bytes_per_launch: <int>'), or None."""
+    lines 'dram_bytes_per_launch: <int>' and 'launches_per_step: <int>'), or None when
+    there is none or it was taken with another split of the step into launches."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{wl}.txt")
+    found, split = None, 1
     try:
         for line in open(path):
             if line.startswith("dram_bytes_per_launch:"):
-                return int(float(line.split(":", 1)[1]))
+                found = int(float(line.split(":", 1)[1]))
+            elif line.startswith("launches_per_step:"):
+                split = int(line.split(":", 1)[1])
     except Exception:
-        pass
-    return None
+        return None
+    return found if split == launches_per_step else None
 
 
 def cpu_oracle_sample(rp, col, sources, w, eps, threads):
@@ -301,17 +305,27 @@ def run_fora(args):
     phase = {"ms_push": 0.0, "ms_residual": 0.0, "ms_walk": 0.0, "ms_topk": 0.0}
     counters = {"launches": 0, "walks": 0, "moves": 0}
 
+    def part_bounds(nsrc):
+        """The library's split of a batch into pipeline parts (at least 32 sources each):
+        each part has its own launches and its own phase times in its stats."""
+        parts = max(1, min(g.tuning("pipeline"), nsrc // 32))
+        return [(nsrc * k // parts, nsrc * (k + 1) // parts) for k in range(parts)]
+
     def collect(step, st, ms):
+        bounds = part_bounds(len(st))
         rounds = max(s.push_rounds for s in st)
-        # push: the seed, then (rounds + 1) passes of the loop body (spread, take,
-        # advance); residuals 4, walks 1, estimate 1, top-k select 19
-        counters["launches"] += 1 + 3 * (rounds + 1) + 4 + 1 + 1 + 19
+        for lo, hi in bounds:
+            r_k = max(s.push_rounds for s in st[lo:hi])
+            # push: the seed, then (rounds + 1) passes of the loop body (spread, take,
+            # advance); residuals 4, walks 1, estimate 1, top-k select 19
+            counters["launches"] += 1 + 3 * (r_k + 1) + 4 + 1 + 1 + 19
         if model is not None:
-            counters["launches"] += 3  # features, forward, r_max
+            counters["launches"] += 3  # features, forward, r_max (whole batch)
+        # kernel time of each phase, summed over the parts (parts overlap in time)
         for key in phase:
-            phase[key] += getattr(st[0], key)
-        walk_ms.append(st[0].ms_walk)
-        push_ms.append(st[0].ms_push)
+            phase[key] += sum(getattr(st[lo], key) for lo, _ in bounds)
+        walk_ms.append(sum(st[lo].ms_walk for lo, _ in bounds))
+        push_ms.append(sum(st[lo].ms_push for lo, _ in bounds))
         push_bytes.append(PUSH_BYTES_PER_EDGE * sum(s.edge_pushes for s in st) +
                           PUSH_BYTES_PER_VERTEX * sum(s.pushes for s in st))
         nw = sum(s.walks for s in st)
@@ -322,12 +336,13 @@ def run_fora(args):
         walk_bytes.append(WALK_BYTES_PER_MOVE * ns + WALK_BYTES_PER_WALK * nw +
                           WALK_BYTES_PER_ENTRY * nr)
         if args.stats:
-            print(json.dumps({"step": step, "ms": ms, "rounds": rounds,
+            print(json.dumps({"step": step, "ms": ms, "rounds": rounds, "parts": len(bounds),
                               "pushes": sum(s.pushes for s in st),
                               "edge_pushes": sum(s.edge_pushes for s in st),
                               "residual_nodes": nr, "walks": nw, "moves": ns,
                               "rmax_mean": sum(s.rmax for s in st) / len(st),
-                              **{k_: getattr(st[0], k_) for k_ in phase}}), file=sys.stderr)
+                              **{k_: sum(getattr(st[lo], k_) for lo, _ in bounds)
+                                 for k_ in phase}}), file=sys.stderr)
 
     step_ms = timed(model, args.steps, collect)
     torch.cuda.synchronize()
@@ -371,11 +386,17 @@ def run_fora(args):
            "d2h_bytes_per_step": B * k * (4 + 8)}
 
     peak, peak_kind = measured_peak_hbm()
-    achieved = (sum(walk_bytes) / len(walk_bytes)) / (statistics.mean(walk_ms) / 1e3) / 1e9
+    # per launch of the walk kernel (one per pipeline part of a step): the launches'
+    # algorithmic bytes over their summed CUDA-event durations
+    launches_per_step = len(part_bounds(B))
+    bytes_per_launch = sum(walk_bytes) / (len(walk_bytes) * launches_per_step)
+    ms_per_launch = sum(walk_ms) / (len(walk_ms) * launches_per_step)
+    achieved = bytes_per_launch / (ms_per_launch / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": "k_walks", "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": profiled_traffic("k_walks", args.workload),
-                "algorithmic_bytes_per_launch": sum(walk_bytes) / len(walk_bytes)}
+                "traffic": profiled_traffic("k_walks", args.workload, launches_per_step),
+                "algorithmic_bytes_per_launch": bytes_per_launch,
+                "launches_per_step": launches_per_step}
     # the push phase (all its rounds: spread, take, advance) against the same peak
     achieved_push = (sum(push_bytes) / len(push_bytes)) / (statistics.mean(push_ms) / 1e3) / 1e9
     roofline_push = {"bound": "hbm", "kernels": "k_push_spread+k_push_take+k_push_advance",

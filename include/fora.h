@@ -347,19 +347,30 @@ int fora_threshold_debug(const double *r, const double *rmax, const uint32_t *d,
  * "push_host_loop" (0 or 1, default 0): 1 launches the push rounds from a host loop with
  * one device-to-host read per round, instead of the CUDA graph whose conditional while-node
  * runs them on the device; the kernels are the same (a profiler that cannot look inside
- * conditional graph nodes sees each of them).  Unknown keys and out-of-range values
- * return FORA_ERR_BAD_ARG.
+ * conditional graph nodes sees each of them).  "pipeline" (1..4, default 1): a batched
+ * query of B >= 64 sources runs as that many parts (at least 32 sources each), each on
+ * its own workspace, stream and host thread, part k's push starting when part k-1's push
+ * has finished, so one part's walk phase runs beside the next part's push; the call's
+ * stream waits for all parts, and each part's stats carry that part's phase times.
+ * Results do not depend on it.  Unknown keys and out-of-range values return
+ * FORA_ERR_BAD_ARG.
  */
 int fora_graph_tune(fora_graph *g, const char *key, int64_t value);
+
+/* The current value of a fora_graph_tune key (as set, or as the autotuner chose it).
+ * Returns FORA_ERR_BAD_ARG for an unknown key or a null pointer. */
+int fora_graph_tuning(fora_graph *g, const char *key, int64_t *value);
 
 /*
  * Autotuner over the launch shapes of fora_graph_tune: runs the batched query on the
  * given sources (HOST array, a representative batch) once to warm up, then with
  * spread_width 1, 2, 4, 8, 16 keeping the fastest push phase, then with walk_blocks
  * 4, 5, 6 ("walk_blocks": resident 256-thread walk blocks per SM, i.e. the register
- * budget of the walk kernel) keeping the fastest walk phase.  The choices stay set on
- * the graph and are returned (either pointer may be NULL).  Results of queries do not
- * depend on them.
+ * budget of the walk kernel) keeping the fastest walk phase (both with "pipeline" 1),
+ * then, for nsrc >= 64, "pipeline" 1 or 2 by the whole batch's time (the faster of two
+ * runs each).  The choices stay set on the graph; spread_width and walk_blocks are
+ * returned (either pointer may be NULL), all of them through fora_graph_tuning.
+ * Results of queries do not depend on them.
  */
 int fora_graph_autotune(fora_graph *g, const fora_params *params, const int32_t *sources,
                         int32_t nsrc, int32_t *spread_width, int32_t *walk_blocks, void *stream);

@@ -161,6 +161,8 @@ def load():
         L.fora_graph_autotune.argtypes = [P, ctypes.POINTER(Params), P, i32, P, P, P]
         L.fora_graph_tune.restype = I
         L.fora_graph_tune.argtypes = [P, ctypes.c_char_p, i64]
+        L.fora_graph_tuning.restype = I
+        L.fora_graph_tuning.argtypes = [P, ctypes.c_char_p, P]
         L.fora_last_error.restype = ctypes.c_char_p
         L.fora_last_error.argtypes = []
         _lib = L
@@ -228,14 +230,22 @@ class Graph:
         """Set a launch-shape parameter (fora_graph_tune); results do not depend on it."""
         _check(load().fora_graph_tune(self._h, key.encode(), int(value)))
 
+    def tuning(self, key: str) -> int:
+        """The current value of a launch-shape parameter (fora_graph_tuning)."""
+        v = ctypes.c_int64()
+        _check(load().fora_graph_tuning(self._h, key.encode(), ctypes.byref(v)))
+        return v.value
+
     def autotune(self, sources, params: Params, stream=None):
-        """fora_graph_autotune on a representative batch -> {spread_width, walk_blocks}."""
+        """fora_graph_autotune on a representative batch -> {spread_width, walk_blocks,
+        pipeline}."""
         src = np.ascontiguousarray(sources, dtype=np.int32)
         sw, wb = ctypes.c_int32(), ctypes.c_int32()
         _check(load().fora_graph_autotune(self._h, ctypes.byref(params), src.ctypes.data,
                                           len(src), ctypes.byref(sw), ctypes.byref(wb),
                                           _stream_ptr(stream)))
-        return {"spread_width": sw.value, "walk_blocks": wb.value}
+        return {"spread_width": sw.value, "walk_blocks": wb.value,
+                "pipeline": self.tuning("pipeline")}
 
     def info(self):
         n, m, d = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()

@@ -2,12 +2,14 @@
 // the per-graph workspace, and the phase sequence of a (batched) query.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "fora.h"
@@ -195,7 +197,14 @@ int fora::reserve_workspace(fora_graph* g, Workspace* w, int nsrc) {
 int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
                        const int32_t* sources, int nsrc, int32_t* out_ids, double* out_vals,
                        fora_stats* st, const fora_debug_io* dbg, uint32_t dbg_flags,
-                       cudaStream_t stream, RmaxSource rsrc) {
+                       cudaStream_t stream, RmaxSource rsrc, const PipeHook* hook) {
+  // a pipelined part always signals the next part, also when it stops early
+  struct SignalOnExit {
+    PipeLink* link;
+    ~SignalOnExit() {
+      if (link) link->signal(false);
+    }
+  } signal_on_exit{hook ? hook->after : nullptr};
   Resolved rp;
   int rc = resolve(g, p, &rp);
   if (rc) return rc;
@@ -266,6 +275,8 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
     b.walk_blocks = g->tune.walk_blocks;
   }
 
+  if (hook && hook->before && hook->before->wait())  // the earlier part's push is done
+    CUDA_TRY(cudaStreamWaitEvent(stream, hook->before->ev, 0));
   const bool timed = st != nullptr;
   if (timed) CUDA_TRY(cudaEventRecord(w->ev[0], stream));
 
@@ -302,6 +313,10 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
       CUDA_TRY(cudaMemcpyAsync(dbg->residue, w->r, N * sizeof(double), cudaMemcpyDeviceToDevice, stream));
   }
   if (timed) CUDA_TRY(cudaEventRecord(w->ev[1], stream));
+  if (hook && hook->after) {
+    CUDA_TRY(cudaEventRecord(hook->after->ev, stream));
+    hook->after->signal(true);
+  }
 
   // ---- walks (Alg. 2) ----
   CUDA_TRY(launch_residuals(gd, b, stream));
@@ -361,9 +376,85 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
 
 namespace {
 
+// A batch in `parts` parts, each on its own workspace and stream, driven by its own host
+// thread; part k's push waits for part k-1's push to finish, so part k-1's walks (bound
+// by instruction issue) run beside part k's push (bound by L2 reductions).  The caller's
+// stream waits for every part, so work queued on it afterwards sees the results.
+constexpr int kMinPartSources = 32;
+
+int run_batch_pipelined(fora_graph* g, const fora_params* p, const int32_t* sources, int nsrc,
+                        int32_t* out_ids, double* out_vals, fora_stats* st, cudaStream_t stream,
+                        RmaxSource rsrc, int parts) {
+  CUDA_TRY(cudaSetDevice(g->device));
+  {
+    std::lock_guard<std::mutex> lock(g->mu);
+    for (int k = 0; k < parts; ++k)
+      if (!g->pipe_stream[k])
+        CUDA_TRY(cudaStreamCreateWithFlags(&g->pipe_stream[k], cudaStreamNonBlocking));
+  }
+  cudaEvent_t start = nullptr;
+  CUDA_TRY(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+  std::vector<PipeLink> links(parts);
+  std::vector<cudaEvent_t> ends(parts, nullptr);
+  cudaError_t e = cudaEventRecord(start, stream);
+  for (int k = 0; k < parts && e == cudaSuccess; ++k) {
+    e = cudaEventCreateWithFlags(&links[k].ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ends[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(g->pipe_stream[k], start, 0);
+  }
+  std::vector<int> rcs(parts, FORA_OK);
+  std::vector<std::string> errs(parts);
+  if (e == cudaSuccess) {
+    std::vector<std::thread> th;
+    const int k_out = p->k;
+    for (int k = 0; k < parts; ++k) {
+      const int lo = (int)((int64_t)nsrc * k / parts), hi = (int)((int64_t)nsrc * (k + 1) / parts);
+      th.emplace_back([&, k, lo, hi] {
+        PipeHook hook{k > 0 ? &links[k - 1] : nullptr, k + 1 < parts ? &links[k] : nullptr};
+        RmaxSource rs;
+        rs.host = rsrc.host ? rsrc.host + lo : nullptr;
+        rs.device = rsrc.device ? rsrc.device + lo : nullptr;
+        if (cudaSetDevice(g->device) != cudaSuccess) {
+          if (hook.after) hook.after->signal(false);
+          rcs[k] = FORA_ERR_CUDA;
+          errs[k] = "cudaSetDevice failed in a pipeline part";
+          return;
+        }
+        rcs[k] = run_batch_ws(g, &g->pipe_ws[k], p, sources + lo, hi - lo,
+                              out_ids ? out_ids + (size_t)lo * k_out : nullptr,
+                              out_vals ? out_vals + (size_t)lo * k_out : nullptr,
+                              st ? st + lo : nullptr, nullptr, 0, g->pipe_stream[k], rs, &hook);
+        if (rcs[k]) errs[k] = g_err;
+      });
+    }
+    for (auto& t : th) t.join();
+    for (int k = 0; k < parts && e == cudaSuccess; ++k) {
+      e = cudaEventRecord(ends[k], g->pipe_stream[k]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, ends[k], 0);
+    }
+  }
+  cudaEventDestroy(start);
+  for (int k = 0; k < parts; ++k) {
+    if (links[k].ev) cudaEventDestroy(links[k].ev);
+    if (ends[k]) cudaEventDestroy(ends[k]);
+  }
+  for (int k = 0; k < parts; ++k)
+    if (rcs[k]) return fail(rcs[k], "%s", errs[k].c_str());
+  CUDA_TRY(e);
+  return FORA_OK;
+}
+
 int run_batch(fora_graph* g, const fora_params* p, const int32_t* sources, int nsrc,
               int32_t* out_ids, double* out_vals, fora_stats* st, const fora_debug_io* dbg,
               uint32_t dbg_flags, cudaStream_t stream, RmaxSource rsrc = RmaxSource()) {
+  int parts;
+  {
+    std::lock_guard<std::mutex> lock(g->mu);
+    parts = g->tune.pipeline;
+  }
+  parts = std::min(parts, nsrc / kMinPartSources);
+  if (!dbg && parts > 1)
+    return run_batch_pipelined(g, p, sources, nsrc, out_ids, out_vals, st, stream, rsrc, parts);
   return run_batch_ws(g, &g->ws, p, sources, nsrc, out_ids, out_vals, st, dbg, dbg_flags, stream,
                       rsrc);
 }
@@ -450,6 +541,11 @@ void fora_graph_destroy(fora_graph* g) {
     std::lock_guard<std::mutex> lock(g->ws.mu);
     cudaSetDevice(g->device);
     g->ws.release();
+    for (int k = 0; k < kMaxPipeline; ++k) {
+      std::lock_guard<std::mutex> plock(g->pipe_ws[k].mu);
+      g->pipe_ws[k].release();
+      if (g->pipe_stream[k]) cudaStreamDestroy(g->pipe_stream[k]);
+    }
     dfree(g->row);
     dfree(g->col);
     dfree(g->colp);
@@ -623,6 +719,11 @@ int fora_graph_tune(fora_graph* g, const char* key, int64_t value) {
   if (strcmp(key, "walk_blocks") == 0) {
     if (value < 4 || value > 6) return fail(FORA_ERR_BAD_ARG, "walk_blocks must be 4, 5 or 6");
     g->tune.walk_blocks = (int)value;
+    return FORA_OK;
+  }
+  if (strcmp(key, "pipeline") == 0) {
+    if (value < 1 || value > kMaxPipeline) return fail(FORA_ERR_BAD_ARG, "pipeline must be in [1, %d]", kMaxPipeline);
+    g->tune.pipeline = (int)value;
     return FORA_OK;
   }
   if (strcmp(key, "push_host_loop") == 0) {
@@ -903,6 +1004,12 @@ int fora_graph_autotune(fora_graph* g, const fora_params* params, const int32_t*
     *walk_ms = st[0].ms_walk;
     return FORA_OK;
   };
+  int parts_asked;
+  {
+    std::lock_guard<std::mutex> lock(g->mu);
+    parts_asked = g->tune.pipeline;
+    g->tune.pipeline = 1;  // phase times below are those of the whole batch
+  }
   float pm = 0, wm = 0;
   int rc = run(&pm, &wm);  // warm-up: workspace and push-loop graph
   if (rc) return rc;
@@ -936,9 +1043,51 @@ int fora_graph_autotune(fora_graph* g, const fora_params* params, const int32_t*
     std::lock_guard<std::mutex> lock(g->mu);
     g->tune.walk_blocks = best_wb;
   }
+  // pipeline: 1 or 2 parts (when the batch allows two), by the whole batch's time
+  int best_parts = 1;
+  if (nsrc >= 2 * kMinPartSources || parts_asked > 1) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    float best_total = 0;
+    for (int parts = 1; parts <= 2 && rc == FORA_OK; ++parts) {
+      {
+        std::lock_guard<std::mutex> lock(g->mu);
+        g->tune.pipeline = parts;
+      }
+      float t = 0;
+      for (int rep = 0; rep < 2 && rc == FORA_OK; ++rep) {  // the faster of two runs
+        cudaEventRecord(e0, (cudaStream_t)stream);
+        rc = run(&pm, &wm);
+        cudaEventRecord(e1, (cudaStream_t)stream);
+        float ms = 0;
+        if (rc == FORA_OK && cudaEventSynchronize(e1) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && (rep == 0 || ms < t))
+          t = ms;
+      }
+      if (parts == 1 || t < best_total) { best_total = t; best_parts = parts; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+  }
+  {
+    std::lock_guard<std::mutex> lock(g->mu);
+    g->tune.pipeline = best_parts;
+  }
   if (spread_width) *spread_width = best_sw;
   if (walk_blocks) *walk_blocks = best_wb;
   return FORA_OK;
+}
+
+int fora_graph_tuning(fora_graph* g, const char* key, int64_t* value) {
+  if (!g || !key || !value) return fail(FORA_ERR_BAD_ARG, "null graph, key or value");
+  std::lock_guard<std::mutex> lock(g->mu);
+  if (strcmp(key, "spread_width") == 0) { *value = g->tune.spread_width; return FORA_OK; }
+  if (strcmp(key, "walk_blocks") == 0) { *value = g->tune.walk_blocks; return FORA_OK; }
+  if (strcmp(key, "pipeline") == 0) { *value = g->tune.pipeline; return FORA_OK; }
+  if (strcmp(key, "push_host_loop") == 0) { *value = g->tune.push_host_loop; return FORA_OK; }
+  return fail(FORA_ERR_BAD_ARG, "unknown tuning key '%s'", key);
 }
 
 const char* fora_last_error(void) { return g_err.c_str(); }

@@ -132,6 +132,7 @@ struct Tuning {
   int spread_width = 1;
   int walk_blocks = 4;
   int push_host_loop = 0;  // 1: rounds launched from a host loop instead of the graph
+  int pipeline = 1;        // parts of a batch run on their own streams, pushes staggered
 };
 
 // capi.cu: record a failure for fora_last_error() and return `code`.

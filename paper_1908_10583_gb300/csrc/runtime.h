@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <condition_variable>
 #include <mutex>
 
 #include "fora.h"
@@ -103,6 +104,41 @@ struct Workspace {
 
 }  // namespace fora
 
+namespace fora {
+
+// Ordering between consecutive parts of a pipelined batch: the later part's push waits
+// on the device until the earlier part's push is done (so the earlier part's walks run
+// beside the later part's push).  The earlier part's host thread records `ev` after
+// enqueueing its push and signals; it signals without recording if it stops early.
+struct PipeLink {
+  std::mutex m;
+  std::condition_variable cv;
+  bool signalled = false;
+  bool recorded = false;
+  cudaEvent_t ev = nullptr;
+  void signal(bool rec) {
+    {
+      std::lock_guard<std::mutex> lk(m);
+      if (signalled) return;
+      signalled = true;
+      recorded = rec;
+    }
+    cv.notify_all();
+  }
+  bool wait() {  // true if ev was recorded
+    std::unique_lock<std::mutex> lk(m);
+    cv.wait(lk, [&] { return signalled; });
+    return recorded;
+  }
+};
+struct PipeHook {
+  PipeLink* before = nullptr;  // wait for this one before the push
+  PipeLink* after = nullptr;   // signal this one after enqueueing the push
+};
+constexpr int kMaxPipeline = 4;
+
+}  // namespace fora
+
 struct fora_graph {
   int64_t n = 0, m = 0, max_deg = 0;
   uint64_t hub_chunks = 0;  // sum over nodes with d > kHubChunk of ceil(d / kHubChunk)
@@ -116,6 +152,9 @@ struct fora_graph {
   fora::Tuning tune;
   std::mutex mu;              // guards `tune`
   fora::Workspace ws;         // the graph's own entry points
+  // parts of a pipelined batch: a workspace and a stream each
+  fora::Workspace pipe_ws[fora::kMaxPipeline];
+  cudaStream_t pipe_stream[fora::kMaxPipeline] = {};
   fora::GraphDev dev() const { return fora::GraphDev{n, m, row, col, colp, colbits}; }
 };
 
@@ -132,6 +171,6 @@ int reserve_workspace(fora_graph* g, Workspace* w, int nsrc);
 int run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p, const int32_t* sources,
                  int nsrc, int32_t* out_ids, double* out_vals, fora_stats* st,
                  const fora_debug_io* dbg, uint32_t dbg_flags, cudaStream_t stream,
-                 RmaxSource rsrc);
+                 RmaxSource rsrc, const PipeHook* hook = nullptr);
 
 }  // namespace fora

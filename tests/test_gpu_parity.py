@@ -307,6 +307,8 @@ def test_autotuner_and_launch_shapes_do_not_change_results(rmat14):
     ref_ids, ref_vals, ref_st, ref = run_debug(g, sources, p)
     choice = g.autotune(sources, p)
     assert choice["spread_width"] in (1, 2, 4, 8, 16) and choice["walk_blocks"] in (4, 5, 6)
+    assert choice["pipeline"] == 1  # 12 sources: too few to split
+    assert g.tuning("walk_blocks") == choice["walk_blocks"]
     for sw, wb in [(1, 4), (16, 5), (3, 6), (choice["spread_width"], choice["walk_blocks"])]:
         g.tune("spread_width", sw)
         g.tune("walk_blocks", wb)
@@ -379,3 +381,25 @@ def test_device_frontier_test_equals_fp64_comparison():
     bad = np.flatnonzero(got != want)
     assert bad.size == 0, [(R[i], RM[i], D[i], got[i]) for i in bad[:5]]
     assert want.any() and (~want).any()
+
+
+def test_pipelined_batch_equals_one_part(rmat14):
+    """pipeline=2 and 3 (parts on their own streams, pushes staggered) give the same walk
+    counts and top-k as one part, source by source (same Philox counters)."""
+    rp, col, g = rmat14
+    n = len(rp) - 1
+    sources = inputs.uniform_sources(n, 100, 6161)
+    p = fora.Params.make(k=50, seed=10)
+    ids1, vals1, st1 = g.ssppr_batch(sources, p)
+    try:
+        for parts in (2, 3):
+            g.tune("pipeline", parts)
+            ids2, vals2, st2 = g.ssppr_batch(sources, p)
+            assert [s.walks for s in st2] == [s.walks for s in st1]
+            assert [s.pushes for s in st2] == [s.pushes for s in st1]
+            np.testing.assert_allclose(vals2, vals1, rtol=0, atol=2e-12)
+            assert (ids2 == ids1).mean() > 0.99  # ids may swap only between near-equal values
+    finally:
+        g.tune("pipeline", 1)
+    with pytest.raises(fora.FORAError):
+        g.tune("pipeline", 5)

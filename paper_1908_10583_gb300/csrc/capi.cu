@@ -269,10 +269,12 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
   b.blk_cnt = w->blk;
   b.blk_walks = w->blk + w->residual_grid;
   b.residual_grid = w->residual_grid;
+  bool host_loop;
   {
     std::lock_guard<std::mutex> tlock(g->mu);
     b.spread_width = g->tune.spread_width;
     b.walk_blocks = g->tune.walk_blocks;
+    host_loop = g->tune.push_host_loop != 0;
   }
 
   if (hook && hook->before && hook->before->wait())  // the earlier part's push is done
@@ -290,7 +292,7 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
     CUDA_TRY(cudaMemsetAsync(w->work, 0, 32 * sizeof(unsigned long long), stream));
     CUDA_TRY(cudaMemsetAsync(w->slot_cnt, 0, 4 * (size_t)nsrc * sizeof(uint32_t), stream));
     CUDA_TRY(launch_push_seed(gd, b, stream));
-    if (g->tune.push_host_loop) {
+    if (host_loop) {
       // the same round kernels launched one round at a time from the host (for profilers
       // that cannot look inside conditional graph nodes); one host round trip per round
       uint32_t go = 1;

@@ -524,6 +524,13 @@ int fora_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col, uin
       e = cudaMemcpy(g->colp, packed.data(), words * sizeof(uint32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) g->colbits = bits;
   }
+  if (e == cudaSuccess) {  // reciprocal out-degrees (every d >= 1 here)
+    std::vector<double> invd((size_t)n);
+    for (int64_t v = 0; v < n; ++v) invd[v] = 1.0 / (double)(row[v + 1] - row[v]);
+    e = cudaMalloc(&g->invd, (size_t)n * sizeof(double));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(g->invd, invd.data(), (size_t)n * sizeof(double), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaMalloc(&g->indeg, (size_t)n * sizeof(uint32_t));
   if (e == cudaSuccess) {
     const GraphDev gd = g->dev();
@@ -552,6 +559,7 @@ void fora_graph_destroy(fora_graph* g) {
     dfree(g->col);
     dfree(g->colp);
     dfree(g->indeg);
+    dfree(g->invd);
   }
   delete g;
 }

@@ -45,6 +45,7 @@ struct GraphDev {
   // smaller footprint keeps more of the graph in L2 beside the walk tallies.
   const uint32_t* colp;
   int colbits;
+  const double* invd;   // [n] RN(1 / d(v)): the push increment is a product, not a quotient
 };
 
 // Target e of a bit-packed column array (two 32-bit words always readable).

@@ -11,7 +11,10 @@
 //                   streaming pass over their residues; each crossing node is appended
 //                   to its source's region and taken at once:
 //                   a_u = r(u); reserve(u) += alpha a_u; r(u) = 0;
-//                   inc_u = (1 - alpha) a_u / d(u)   (the first half of round t+1).
+//                   inc_u = (1 - alpha) a_u / d(u)   (the first half of round t+1),
+//                   computed as RN(RN((1 - alpha) a_u) * RN(1 / d(u))) with the
+//                   graph's reciprocal degrees (within an ulp or so of the quotient;
+//                   this GPU's FP64 division costs about ten FP64 instructions).
 //   k_push_advance  one block: per-source prefix of the new frontier's groups and hub
 //                   items, the list of sources still pushing, the loop condition.
 // The take of round t+1 happens after every add of round t (kernel boundary), so
@@ -371,12 +374,13 @@ __global__ void __launch_bounds__(kTakeThreads, 3) k_push_take(GraphDev g, Batch
         const uint32_t e = e0 + lane;
         const bool live = e < mine;
         uint32_t u = 0, dk = 1;
-        double a = 0.0, rs = 0.0;
+        double a = 0.0, rs = 0.0, inv = 0.0;
         if (live) {
           u = st_u[e];
           dk = st_d[e];
           a = st_a[e];
           rs = b.res[g0 + u];
+          inv = g.invd[u];
         }
         const uint32_t nch = live ? hub_chunks_of(dk) : 0u;
         const uint32_t nch_incl = hsum ? warp_incl_scan(nch) : 0u;  // lower entries first
@@ -387,7 +391,7 @@ __global__ void __launch_bounds__(kTakeThreads, 3) k_push_take(GraphDev g, Batch
           b.res[gi] = __dadd_rn(rs, __dmul_rn(alpha, a));
           const unsigned long long qi = g0 + qb + e;
           qn[qi] = ((unsigned long long)s << 32) | u;
-          b.fa[qi] = __ddiv_rn(__dmul_rn(beta, a), (double)dk);
+          b.fa[qi] = __dmul_rn(__dmul_rn(beta, a), inv);  // (1 - alpha) a / d
           const unsigned long long hbase =
               (unsigned long long)s * b.hub_stride + hp + (nch_incl - nch);
           for (uint32_t c = 0; c < nch; ++c) hn[hbase + c] = (qi << kHubChunkBits) | c;

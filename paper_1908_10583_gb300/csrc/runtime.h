@@ -147,6 +147,7 @@ struct fora_graph {
   uint32_t* colp = nullptr;   // col bit-packed to colbits bits per target (0: not packed)
   int colbits = 0;
   uint32_t* indeg = nullptr;  // in-degrees (features of the learned r_max)
+  double* invd = nullptr;     // RN(1 / d(v)) per node
   int device = 0;
   int num_sms = 0;
   fora::Tuning tune;
@@ -155,7 +156,7 @@ struct fora_graph {
   // parts of a pipelined batch: a workspace and a stream each
   fora::Workspace pipe_ws[fora::kMaxPipeline];
   cudaStream_t pipe_stream[fora::kMaxPipeline] = {};
-  fora::GraphDev dev() const { return fora::GraphDev{n, m, row, col, colp, colbits}; }
+  fora::GraphDev dev() const { return fora::GraphDev{n, m, row, col, colp, colbits, invd}; }
 };
 
 namespace fora {

@@ -411,23 +411,30 @@ int run_batch_pipelined(fora_graph* g, const fora_params* p, const int32_t* sour
     const int k_out = p->k;
     for (int k = 0; k < parts; ++k) {
       const int lo = (int)((int64_t)nsrc * k / parts), hi = (int)((int64_t)nsrc * (k + 1) / parts);
-      th.emplace_back([&, k, lo, hi] {
-        PipeHook hook{k > 0 ? &links[k - 1] : nullptr, k + 1 < parts ? &links[k] : nullptr};
-        RmaxSource rs;
-        rs.host = rsrc.host ? rsrc.host + lo : nullptr;
-        rs.device = rsrc.device ? rsrc.device + lo : nullptr;
-        if (cudaSetDevice(g->device) != cudaSuccess) {
-          if (hook.after) hook.after->signal(false);
-          rcs[k] = FORA_ERR_CUDA;
-          errs[k] = "cudaSetDevice failed in a pipeline part";
-          return;
-        }
-        rcs[k] = run_batch_ws(g, &g->pipe_ws[k], p, sources + lo, hi - lo,
-                              out_ids ? out_ids + (size_t)lo * k_out : nullptr,
-                              out_vals ? out_vals + (size_t)lo * k_out : nullptr,
-                              st ? st + lo : nullptr, nullptr, 0, g->pipe_stream[k], rs, &hook);
-        if (rcs[k]) errs[k] = g_err;
-      });
+      try {
+        th.emplace_back([&, k, lo, hi] {
+          PipeHook hook{k > 0 ? &links[k - 1] : nullptr, k + 1 < parts ? &links[k] : nullptr};
+          RmaxSource rs;
+          rs.host = rsrc.host ? rsrc.host + lo : nullptr;
+          rs.device = rsrc.device ? rsrc.device + lo : nullptr;
+          if (cudaSetDevice(g->device) != cudaSuccess) {
+            if (hook.after) hook.after->signal(false);
+            rcs[k] = FORA_ERR_CUDA;
+            errs[k] = "cudaSetDevice failed in a pipeline part";
+            return;
+          }
+          rcs[k] = run_batch_ws(g, &g->pipe_ws[k], p, sources + lo, hi - lo,
+                                out_ids ? out_ids + (size_t)lo * k_out : nullptr,
+                                out_vals ? out_vals + (size_t)lo * k_out : nullptr,
+                                st ? st + lo : nullptr, nullptr, 0, g->pipe_stream[k], rs, &hook);
+          if (rcs[k]) errs[k] = g_err;
+        });
+      } catch (...) {  // no thread for part k: release every waiter, run no further part
+        for (auto& l : links) l.signal(false);
+        rcs[k] = FORA_ERR_CUDA;
+        errs[k] = "could not start a host thread for a pipeline part";
+        break;
+      }
     }
     for (auto& t : th) t.join();
     for (int k = 0; k < parts && e == cudaSuccess; ++k) {

@@ -357,6 +357,81 @@ int oracle_walk_phase_zero_hop(int64_t n, const int64_t *row_ptr, const int32_t 
   return ORACLE_OK;
 }
 
+/*
+ * FORA+ walk index (Section 3.3).  After the push every residue satisfies
+ * r(v) <= RN(r_max * d(v)), so a query needs at most
+ *     omega_max(v) = ceil(RN(RN(r_max * d(v)) * C))
+ * walks from v (Eq. index-rwnum with the same FP64 operations as omega_v, so that
+ * omega_v <= omega_max(v) holds exactly).  The index stores, for every v, the end
+ * nodes of walks j = 0 .. omega_max(v) - 1 from v, walk j reading the Philox stream
+ * with counter (c, j, v, s_index), the same walk definition as oracle_walk_phase.
+ * off[n + 1] is the exclusive prefix of omega_max; dest[off[v] + j] is the end of walk
+ * j from v.  Returns the total number of walks (off[n]) when it is <= cap and dest is
+ * filled; with cap smaller than that it fills off only and returns the total, negated
+ * error codes otherwise.
+ */
+int64_t oracle_walk_index(int64_t n, const int64_t *row_ptr, const int32_t *col, double alpha,
+                          double walk_scale, double rmax, uint64_t seed, uint32_t s_index,
+                          int64_t *off, int32_t *dest, int64_t cap) {
+  int rc = check_graph(n, row_ptr, col);
+  if (rc) return rc;
+  if (!(alpha > 0.0 && alpha < 1.0) || !(walk_scale > 0.0) || !(rmax > 0.0))
+    return ORACLE_ERR_BAD_ARG;
+  off[0] = 0;
+  for (int64_t v = 0; v < n; ++v) {
+    const double d = (double)(row_ptr[v + 1] - row_ptr[v]);
+    const double omega_max = ceil((rmax * d) * walk_scale);
+    if (omega_max > 4294967295.0) return ORACLE_ERR_WALK_OVERFLOW;
+    off[v + 1] = off[v] + (int64_t)omega_max;
+  }
+  const int64_t total = off[n];
+  if (total > cap) return total;
+  const uint32_t t_alpha = oracle_alpha_threshold(alpha);
+  int64_t steps = 0;
+  for (int64_t v = 0; v < n; ++v) {
+    for (int64_t j = 0; j < off[v + 1] - off[v]; ++j) {
+      walk_stream w;
+      stream_init(&w, (uint32_t)j, (uint32_t)v, s_index, seed);
+      const int64_t end = random_walk(row_ptr, col, t_alpha, &w, (int32_t)v, &steps);
+      if (end < 0) return ORACLE_ERR_WALK_CAP;
+      dest[off[v] + j] = (int32_t)end;
+    }
+  }
+  return total;
+}
+
+/*
+ * Walk phase of Alg. 2 served from a FORA+ index (Section 3.3): for every v with
+ * r(v) > 0, the ends of the first omega_v = ceil(r(v) * C) walks stored for v, each
+ * adding W_v = rint((r(v)/omega_v) * 2^63) to acc[end] and 1 to count[end].  An
+ * omega_v above the index's omega_max(v) is an error (the residue exceeds the index's
+ * r_max).  st->walk_steps stays 0 (no walk is simulated).
+ */
+int oracle_walk_phase_indexed(int64_t n, double walk_scale, const double *residue,
+                              const int64_t *off, const int32_t *dest, uint32_t *count,
+                              uint64_t *acc, oracle_walk_stats *st) {
+  if (n < 1 || !(walk_scale > 0.0)) return ORACLE_ERR_BAD_ARG;
+  oracle_walk_stats local = {0, 0, 0};
+  for (int64_t t = 0; t < n; ++t) { count[t] = 0; acc[t] = 0; }
+  for (int64_t v = 0; v < n; ++v) {
+    if (residue[v] < 0.0) return ORACLE_ERR_BAD_ARG;
+    if (!(residue[v] > 0.0)) continue;
+    const double omega_v = ceil(residue[v] * walk_scale);
+    if (omega_v > (double)(off[v + 1] - off[v])) return ORACLE_ERR_BAD_ARG;
+    const double weight = residue[v] / omega_v;
+    const uint64_t fixed = (uint64_t)nearbyint(ldexp(weight, 63));
+    local.residual_nodes++;
+    local.walks += (int64_t)omega_v;
+    for (int64_t j = 0; j < (int64_t)omega_v; ++j) {
+      const int32_t end = dest[off[v] + j];
+      count[end] += 1;
+      acc[end] += fixed;
+    }
+  }
+  if (st) *st = local;
+  return ORACLE_OK;
+}
+
 /* Zero-hop estimate: pi_hat(t) = (reserve(t) + alpha * r(t)) + acc(t) * 2^-63 */
 void oracle_estimate_zero_hop(int64_t n, const double *reserve, const double *residue,
                               const uint64_t *acc, double alpha, double *est) {

@@ -58,6 +58,8 @@ def parse_args(argv=None):
                     help="skip fora_graph_autotune (launch shapes at their defaults / --tune)")
     ap.add_argument("--plain-sources", type=int, default=16,
                     help="single-source queries timed for the plain-FORA comparison")
+    ap.add_argument("--no-index", action="store_true",
+                    help="skip the FORA+ (walk index, Section 3.3) comparison")
     return ap.parse_args(argv)
 
 
@@ -365,6 +367,32 @@ def run_fora(args):
         for s_ in plain_src:
             g.ssppr(int(s_), params)
         comparison["plain_fora_qps"] = len(plain_src) / (time.perf_counter() - t0)
+    if not args.no_index:
+        # FORA+: the walk phase served from a walk index built for the rule's r_max
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.build_index(params, stream=stream)
+        torch.cuda.synchronize()
+        build_s = time.perf_counter() - t0
+        iparams = fora.Params.from_buffer_copy(params)
+        iparams.flags |= fora.FORA_USE_INDEX
+        g.ssppr_batch(sources(-50), iparams, out_ids=ids, out_vals=vals, stream=stream)
+        idx_ms = []
+        for step in range(args.steps):
+            src = sources(step)
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.ssppr_batch(src, iparams, out_ids=ids, out_vals=vals, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            idx_ms.append(e0.elapsed_time(e1))
+        comparison["fora_plus_qps"] = B * args.steps / (sum(idx_ms) / 1e3)
+        comparison["fora_plus_index"] = {"walks_stored": g.index_info()[2],
+                                         "bytes": g.index_info()[2] * 4 + (n + 1) * 8,
+                                         "build_s": build_s, "rmax": "rule"}
+        g.drop_index()
 
     # end to end through the public API: host sources in, host results out
     h_ids = torch.empty((B, k), dtype=torch.int32, pin_memory=True).numpy()

@@ -73,6 +73,11 @@ extern "C" {
                                 goes to the estimate directly and omega_v = ceil((1-alpha)
                                 r(v) C) walks each first move to a uniform out-neighbour of
                                 v (no stop test at v), carrying (1-alpha) r(v) / omega_v */
+#define FORA_USE_INDEX 0x8u  /* FORA+ (Section 3.3): walk j from v is the j-th walk stored
+                                for v in the graph's walk index (fora_index_build) instead of
+                                a walk simulated on the fly; needs the index's alpha, eps,
+                                delta, p_f, every source's r_max <= the index's, and no
+                                FORA_ZERO_HOP (else FORA_ERR_BAD_ARG) */
 
 typedef struct fora_graph fora_graph; /* opaque: device copy of the CSR + query workspace */
 
@@ -374,6 +379,31 @@ int fora_graph_tuning(fora_graph *g, const char *key, int64_t *value);
  */
 int fora_graph_autotune(fora_graph *g, const fora_params *params, const int32_t *sources,
                         int32_t nsrc, int32_t *spread_width, int32_t *walk_blocks, void *stream);
+
+/*
+ * FORA+ walk index (Section 3.3).  After the push every residue satisfies
+ * r(v) <= r_max * d_out(v), so a query needs at most
+ *   omega_max(v) = ceil(RN64(RN64(r_max * d_out(v)) * C))   (Eq. index-rwnum)
+ * walks from v.  fora_index_build pre-computes omega_max(v) walks from every node of g
+ * for the resolved parameters of params (r_max by the rule of Section 3.2 unless
+ * params->rmax > 0; C = omega / r_sum of Alg. 2), walk j from v reading the Philox stream
+ * with counter (c, j, v, 2^32 - 1) and key params->seed, and keeps their end nodes on the
+ * device (8 bytes per node + 4 bytes per walk), replacing any earlier index.  Queries with
+ * FORA_USE_INDEX then take the first omega_v stored ends of v.  Not safe while queries on g
+ * run.  Errors: FORA_ERR_BAD_ARG (FORA_ZERO_HOP, or an r_max so small that a node gets no
+ * walk), FORA_ERR_WALK_OVERFLOW (2^32 walks or more), FORA_ERR_OOM, FORA_ERR_CUDA.
+ */
+int fora_index_build(fora_graph *g, const fora_params *params, void *stream);
+
+/* The index's r_max, C and number of stored walks (all 0 without an index). */
+int fora_index_info(const fora_graph *g, double *rmax, double *walk_scale, int64_t *entries);
+
+/* Copy the index to HOST arrays: off [n + 1] (exclusive prefix of omega_max), dest
+ * [entries] (dest[off[v] + j] = end of walk j from v).  FORA_ERR_BAD_ARG without an index. */
+int fora_index_export(const fora_graph *g, int64_t *off, uint32_t *dest);
+
+/* Free the index (no-op without one). */
+int fora_index_destroy(fora_graph *g);
 
 /* Message of the calling thread's last failure ("" if none). */
 const char *fora_last_error(void);

@@ -28,6 +28,7 @@ FORA_MAX_K = 4096
 FORA_OUT_DEVICE = 0x1
 FORA_ASYNC = 0x2
 FORA_ZERO_HOP = 0x4
+FORA_USE_INDEX = 0x8
 FORA_DBG_GIVEN_PUSH = 0x1
 FORA_NUM_FEATURES = 16
 FORA_MODEL_PARAMS = 5313
@@ -163,6 +164,14 @@ def load():
         L.fora_graph_tune.argtypes = [P, ctypes.c_char_p, i64]
         L.fora_graph_tuning.restype = I
         L.fora_graph_tuning.argtypes = [P, ctypes.c_char_p, P]
+        L.fora_index_build.restype = I
+        L.fora_index_build.argtypes = [P, ctypes.POINTER(Params), P]
+        L.fora_index_info.restype = I
+        L.fora_index_info.argtypes = [P, P, P, P]
+        L.fora_index_export.restype = I
+        L.fora_index_export.argtypes = [P, P, P]
+        L.fora_index_destroy.restype = I
+        L.fora_index_destroy.argtypes = [P]
         L.fora_last_error.restype = ctypes.c_char_p
         L.fora_last_error.argtypes = []
         _lib = L
@@ -229,6 +238,27 @@ class Graph:
     def tune(self, key: str, value: int):
         """Set a launch-shape parameter (fora_graph_tune); results do not depend on it."""
         _check(load().fora_graph_tune(self._h, key.encode(), int(value)))
+
+    def build_index(self, params: Params, stream=None):
+        """FORA+ walk index (fora_index_build) for these parameters."""
+        _check(load().fora_index_build(self._h, ctypes.byref(params), _stream_ptr(stream)))
+
+    def index_info(self):
+        """(r_max, C, stored walks) of the walk index, zeros without one."""
+        r, c, e = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+        _check(load().fora_index_info(self._h, ctypes.byref(r), ctypes.byref(c), ctypes.byref(e)))
+        return r.value, c.value, e.value
+
+    def index_export(self):
+        """The walk index on the host: (off int64 [n + 1], dest uint32 [entries])."""
+        _, _, entries = self.index_info()
+        off = np.zeros(self.n + 1, dtype=np.int64)
+        dest = np.zeros(max(entries, 1), dtype=np.uint32)
+        _check(load().fora_index_export(self._h, off.ctypes.data, dest.ctypes.data))
+        return off, dest[:entries]
+
+    def drop_index(self):
+        _check(load().fora_index_destroy(self._h))
 
     def tuning(self, key: str) -> int:
         """The current value of a launch-shape parameter (fora_graph_tuning)."""

@@ -215,6 +215,14 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
   const bool out_dev = (p->flags & FORA_OUT_DEVICE) != 0;
   const bool async = (p->flags & FORA_ASYNC) != 0;
   if (async && (!out_dev || st)) return fail(FORA_ERR_BAD_ARG, "FORA_ASYNC needs FORA_OUT_DEVICE and no stats");
+  const bool indexed = (p->flags & FORA_USE_INDEX) != 0;
+  if (indexed) {
+    if (!g->idx_dest) return fail(FORA_ERR_BAD_ARG, "FORA_USE_INDEX without a walk index (fora_index_build)");
+    if ((p->flags & FORA_ZERO_HOP) != 0)
+      return fail(FORA_ERR_BAD_ARG, "the walk index holds plain walks: FORA_USE_INDEX excludes FORA_ZERO_HOP");
+    if (rp.walk_scale != g->idx_scale || rp.alpha != g->idx_alpha)
+      return fail(FORA_ERR_BAD_ARG, "the walk index was built for other alpha / eps / delta / p_f");
+  }
   const bool given = (dbg_flags & FORA_DBG_GIVEN_PUSH) != 0;
   if (given && (!dbg || !dbg->reserve || !dbg->residue))
     return fail(FORA_ERR_BAD_ARG, "FORA_DBG_GIVEN_PUSH needs reserve and residue arrays");
@@ -231,6 +239,8 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
     w->h_rmax[i] = rsrc.host ? rsrc.host[i] : rp.rmax;
     if (!(w->h_rmax[i] > 0.0) || !std::isfinite(w->h_rmax[i]))
       return fail(FORA_ERR_BAD_ARG, "r_max of source %d must be positive and finite", i);
+    if (indexed && !rsrc.device && w->h_rmax[i] > g->idx_rmax)
+      return fail(FORA_ERR_BAD_ARG, "r_max of source %d is above the walk index's r_max", i);
   }
   CUDA_TRY(cudaMemcpyAsync(w->sources, w->h_sources, nsrc * sizeof(int32_t), cudaMemcpyHostToDevice, stream));
   if (rsrc.device)
@@ -323,7 +333,10 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
   // ---- walks (Alg. 2) ----
   CUDA_TRY(launch_residuals(gd, b, stream));
   if (timed) CUDA_TRY(cudaEventRecord(w->ev[2], stream));
-  CUDA_TRY(launch_walks(gd, b, g->num_sms, stream));
+  if (indexed)
+    CUDA_TRY(launch_walks_indexed(gd, b, g->num_sms, g->idx_off, g->idx_dest, stream));
+  else
+    CUDA_TRY(launch_walks(gd, b, g->num_sms, stream));
   if (timed) CUDA_TRY(cudaEventRecord(w->ev[3], stream));
   if (dbg && (dbg->count || dbg->acc))
     CUDA_TRY(launch_unpack_tally(w->tally, dbg->count, reinterpret_cast<unsigned long long*>(dbg->acc), N,
@@ -352,6 +365,8 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
     return fail(FORA_ERR_PUSH_NOT_CONVERGED, "push did not converge in %u rounds", kMaxPushRounds);
   if (*w->h_err & kErrWalkOverflow) return fail(FORA_ERR_WALK_OVERFLOW, "a source needs 2^32 or more walks");
   if (*w->h_err & kErrWalkCap) return fail(FORA_ERR_WALK_CAP, "a walk exceeded %d moves", FORA_MAX_WALK_STEPS);
+  if (*w->h_err & kErrIndexRange)
+    return fail(FORA_ERR_BAD_ARG, "a residue needs more walks than the walk index holds (r_max above the index's)");
   if (st) {
     float ms[4] = {0, 0, 0, 0};
     for (int i = 0; i < 4; ++i) CUDA_TRY(cudaEventElapsedTime(&ms[i], w->ev[i], w->ev[i + 1]));
@@ -567,8 +582,129 @@ void fora_graph_destroy(fora_graph* g) {
     dfree(g->colp);
     dfree(g->indeg);
     dfree(g->invd);
+    dfree(g->idx_off);
+    dfree(g->idx_dest);
   }
   delete g;
+}
+
+int fora_index_build(fora_graph* g, const fora_params* params, void* stream_) {
+  if (!g || !params) return fail(FORA_ERR_BAD_ARG, "null graph or params");
+  if ((params->flags & FORA_ZERO_HOP) != 0)
+    return fail(FORA_ERR_BAD_ARG, "the walk index holds plain walks (no FORA_ZERO_HOP)");
+  Resolved rp;
+  int rc = resolve(g, params, &rp);
+  if (rc) return rc;
+  cudaStream_t stream = (cudaStream_t)stream_;
+  Workspace* w = &g->ws;
+  std::lock_guard<std::mutex> lock(w->mu);
+  CUDA_TRY(cudaSetDevice(g->device));
+  rc = ensure_workspace(g, w, 1);
+  if (rc) return rc;
+  // one slot: residues r(v) = RN(r_max d(v)), whose walk counts are omega_max(v); the
+  // walks' Philox counters carry the source id 2^32 - 1
+  w->h_sources[0] = -1;
+  w->h_rmax[0] = rp.rmax;
+  CUDA_TRY(cudaMemcpyAsync(w->sources, w->h_sources, sizeof(int32_t), cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(cudaMemcpyAsync(w->rmax, w->h_rmax, sizeof(double), cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(cudaMemsetAsync(w->small, 0, 8 * sizeof(unsigned long long), stream));
+  CUDA_TRY(cudaMemsetAsync(w->err, 0, sizeof(uint32_t), stream));
+  CUDA_TRY(cudaMemsetAsync(w->stats, 0, sizeof(SlotStats), stream));
+  const GraphDev gd = g->dev();
+  BatchDev b{};
+  b.nsrc = 1;
+  b.alpha = rp.alpha;
+  b.walk_scale = rp.walk_scale;
+  b.alpha_threshold = rp.alpha_threshold;
+  b.seed = params->seed;
+  b.r = w->r; b.res = w->res; b.tally = w->tally;
+  b.q[0] = w->q[0]; b.q[1] = w->q[1]; b.fa = w->fa;
+  b.hub[0] = w->hub[0]; b.hub[1] = w->hub[1];
+  b.hub_stride = g->hub_chunks;
+  b.slot_cnt = w->slot_cnt;
+  b.gpre = w->pre;
+  b.hpre = w->pre + 2;
+  b.alist = w->alist;
+  b.work = w->work;
+  b.ps = w->ps;
+  b.totals = w->small + 4;
+  b.sources = w->sources; b.rmax = w->rmax; b.stats = w->stats; b.err = w->err;
+  b.wr_entry = w->q[0];
+  b.wr_offset = w->q[1];
+  b.wr_weight = reinterpret_cast<unsigned long long*>(w->fa);
+  b.blk_cnt = w->blk;
+  b.blk_walks = w->blk + w->residual_grid;
+  b.residual_grid = w->residual_grid;
+  {
+    std::lock_guard<std::mutex> tlock(g->mu);
+    b.spread_width = g->tune.spread_width;
+    b.walk_blocks = g->tune.walk_blocks;
+  }
+  CUDA_TRY(launch_index_residue(gd, w->r, rp.rmax, stream));
+  CUDA_TRY(launch_residuals(gd, b, stream));
+  CUDA_TRY(cudaMemcpyAsync(w->h_counters, w->small + 4, 2 * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, stream));
+  CUDA_TRY(cudaMemcpyAsync(w->h_err, w->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
+  CUDA_TRY(cudaStreamSynchronize(stream));
+  if (*w->h_err & kErrWalkOverflow) return fail(FORA_ERR_WALK_OVERFLOW, "the index would need 2^32 or more walks");
+  const unsigned long long nR = w->h_counters[0], W = w->h_counters[1];
+  if (nR != (unsigned long long)g->n)
+    return fail(FORA_ERR_BAD_ARG, "r_max too small for a walk index: a node would get no stored walk");
+  dfree(g->idx_off);
+  dfree(g->idx_dest);
+  g->idx_entries = 0;
+  CUDA_TRY(cudaMalloc(&g->idx_off, ((size_t)g->n + 1) * sizeof(unsigned long long)));
+  CUDA_TRY(cudaMalloc(&g->idx_dest, (size_t)(W ? W : 1) * sizeof(uint32_t)));
+  b.walk_dest = g->idx_dest;
+  cudaError_t e = launch_walks(gd, b, g->num_sms, stream);
+  // the residual offsets of the nodes 0 .. n-1 (every node is an entry), then W
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(g->idx_off, w->q[1], ((size_t)g->n + 1) * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToDevice, stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(w->h_err, w->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess || (*w->h_err & kErrWalkCap)) {
+    dfree(g->idx_off);
+    dfree(g->idx_dest);
+    if (e != cudaSuccess) return fail(FORA_ERR_CUDA, "index walks: %s", cudaGetErrorString(e));
+    return fail(FORA_ERR_WALK_CAP, "an index walk exceeded %d moves", FORA_MAX_WALK_STEPS);
+  }
+  g->idx_entries = (int64_t)W;
+  g->idx_rmax = rp.rmax;
+  g->idx_scale = rp.walk_scale;
+  g->idx_alpha = rp.alpha;
+  g->idx_seed = params->seed;
+  return FORA_OK;
+}
+
+int fora_index_info(const fora_graph* g, double* rmax, double* walk_scale, int64_t* entries) {
+  if (!g) return fail(FORA_ERR_BAD_ARG, "null graph");
+  if (rmax) *rmax = g->idx_dest ? g->idx_rmax : 0.0;
+  if (walk_scale) *walk_scale = g->idx_dest ? g->idx_scale : 0.0;
+  if (entries) *entries = g->idx_dest ? g->idx_entries : 0;
+  return FORA_OK;
+}
+
+int fora_index_export(const fora_graph* g, int64_t* off, uint32_t* dest) {
+  if (!g || !off || !dest) return fail(FORA_ERR_BAD_ARG, "null graph or output");
+  if (!g->idx_dest) return fail(FORA_ERR_BAD_ARG, "the graph has no walk index");
+  CUDA_TRY(cudaSetDevice(g->device));
+  CUDA_TRY(cudaMemcpy(off, g->idx_off, ((size_t)g->n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+  if (g->idx_entries > 0)
+    CUDA_TRY(cudaMemcpy(dest, g->idx_dest, (size_t)g->idx_entries * sizeof(uint32_t),
+                        cudaMemcpyDeviceToHost));
+  return FORA_OK;
+}
+
+int fora_index_destroy(fora_graph* g) {
+  if (!g) return fail(FORA_ERR_BAD_ARG, "null graph");
+  std::lock_guard<std::mutex> lock(g->ws.mu);
+  CUDA_TRY(cudaSetDevice(g->device));
+  dfree(g->idx_off);
+  dfree(g->idx_dest);
+  g->idx_entries = 0;
+  return FORA_OK;
 }
 
 int fora_graph_info(const fora_graph* g, int64_t* n, int64_t* m, int64_t* max_degree) {

@@ -22,6 +22,7 @@ constexpr uint32_t kSortCap = 8192;  // candidates sorted in shared memory at th
 constexpr uint32_t kErrWalkCap = 1u;
 constexpr uint32_t kErrWalkOverflow = 2u;
 constexpr uint32_t kErrPushNotConverged = 4u;
+constexpr uint32_t kErrIndexRange = 8u;  // a residue needs more walks than the index holds
 constexpr uint32_t kMaxPushRounds = 100000u;
 
 // Where the push loop stands: the parity of the current frontier queue, the number of
@@ -96,6 +97,8 @@ struct BatchDev {
   uint64_t seed;
   int zero_hop;              // walk phase with zero-hop pruning (Section 4.1)
   int want_count;            // tally walk counts too (only a debug output reads them)
+  uint32_t* walk_dest;       // non-null: k_walks stores walk g's end in walk_dest[g]
+                             // (building a walk index) instead of tallying it
   double* r;                 // residue, later the estimate
   double* res;               // reserve
   Tally* tally;              // walk ends per (source, node)
@@ -152,6 +155,12 @@ cudaError_t launch_threshold_table(const double* r, const double* rm, const uint
 // walk.cu
 cudaError_t launch_residuals(const GraphDev& g, const BatchDev& b, cudaStream_t st);
 cudaError_t launch_walks(const GraphDev& g, const BatchDev& b, int num_sms, cudaStream_t st);
+// walk.cu, FORA+ (Section 3.3): r[v] = RN(rmax * d(v)) for one slot (the residues whose
+// omega_v are the index's omega_max(v)), and the walk phase served from an index.
+cudaError_t launch_index_residue(const GraphDev& g, double* r, double rmax, cudaStream_t st);
+cudaError_t launch_walks_indexed(const GraphDev& g, const BatchDev& b, int num_sms,
+                                 const unsigned long long* idx_off, const uint32_t* idx_dest,
+                                 cudaStream_t st);
 cudaError_t launch_unpack_tally(const Tally* t, uint32_t* cnt, unsigned long long* acc,
                                 uint64_t count, int num_sms, cudaStream_t st);
 cudaError_t launch_philox_table(const uint32_t* ctr_key, uint32_t* out, int count,

@@ -148,6 +148,12 @@ struct fora_graph {
   int colbits = 0;
   uint32_t* indeg = nullptr;  // in-degrees (features of the learned r_max)
   double* invd = nullptr;     // RN(1 / d(v)) per node
+  // FORA+ walk index (Section 3.3): ends of omega_max(v) walks from every v
+  unsigned long long* idx_off = nullptr;  // [n + 1] exclusive prefix of omega_max
+  uint32_t* idx_dest = nullptr;           // [idx_entries] walk ends
+  int64_t idx_entries = 0;
+  double idx_rmax = 0.0, idx_scale = 0.0, idx_alpha = 0.0;
+  uint64_t idx_seed = 0;
   int device = 0;
   int num_sms = 0;
   fora::Tuning tune;

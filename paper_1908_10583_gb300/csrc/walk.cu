@@ -358,10 +358,15 @@ __global__ void __launch_bounds__(kWalkThreads, kMinBlocks) k_walks(GraphDev g, 
       if (have && !forced) stop = rng.next() < t_alpha;
       const uint32_t stops = __ballot_sync(kFull, stop);
       if (stop) {
-        // the walk stops at x (Section 2.1): count it and add its weight (Alg. 2)
-        Tally* t = b.tally + (unsigned long long)slot * (unsigned long long)g.n + x;
-        if (b.want_count) atomicAdd(&t->cnt, 1u);
-        atomicAdd(&t->acc, wgt);
+        // the walk stops at x (Section 2.1): count it and add its weight (Alg. 2), or
+        // record its end in a walk index (Section 3.3)
+        if (b.walk_dest) {
+          b.walk_dest[cbeg + i] = x;
+        } else {
+          Tally* t = b.tally + (unsigned long long)slot * (unsigned long long)g.n + x;
+          if (b.want_count) atomicAdd(&t->cnt, 1u);
+          atomicAdd(&t->acc, wgt);
+        }
         if (slot != cur_slot) {
           if (steps_here) atomicAdd(&b.stats[cur_slot].walk_steps, steps_here);
           steps_here = 0;
@@ -415,6 +420,70 @@ __global__ void __launch_bounds__(kWalkThreads, kMinBlocks) k_walks(GraphDev g, 
   }
   if (capped) atomicOr(b.err, kErrWalkCap);
   if (steps_here) atomicAdd(&b.stats[cur_slot].walk_steps, steps_here);
+}
+
+// FORA+ (Section 3.3): the residue whose walk count is the index's omega_max(v).
+__global__ void k_index_residue(GraphDev g, double* r, double rmax) {
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long v = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+       v < (unsigned long long)g.n; v += stride)
+    r[v] = __dmul_rn(rmax, (double)(g.row[v + 1] - g.row[v]));
+}
+
+// The walk phase served from a walk index: walk j of residual entry (slot, v) ends at
+// idx_dest[idx_off[v] + j] (the j-th stored walk from v) instead of being simulated.
+// Walks map to entries as in k_walks (chunks of kChunk, a shared-memory map per warp).
+// A walk past v's stored walks (a residue above the index's r_max) sets kErrIndexRange
+// and is skipped.
+__global__ void __launch_bounds__(kWalkThreads) k_walks_indexed(GraphDev g, BatchDev b,
+                                                                const unsigned long long* idx_off,
+                                                                const uint32_t* idx_dest) {
+  __shared__ uint16_t smap[kWalkWarps][kChunk];
+  if (*b.err) return;
+  const unsigned long long W = b.totals[1];
+  const unsigned long long nR = b.totals[0];
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  const unsigned long long nchunks = (W + kChunk - 1) / kChunk;
+  const unsigned long long* off = b.wr_offset;
+  bool out_of_range = false;
+  for (unsigned long long c = warp; c < nchunks; c += nwarps) {
+    const unsigned long long cbeg = c * kChunk;
+    const uint32_t cnt = (uint32_t)min((unsigned long long)kChunk, W - cbeg);
+    const unsigned long long idx0 = warp_find_entry(off, nR, cbeg);
+    unsigned long long idxw = idx0;
+    for (uint32_t rb = 0; rb < cnt; rb += 32) {
+      const unsigned long long gw = cbeg + rb + lane;
+      const unsigned long long o = idxw + lane < nR ? off[idxw + lane] : ~0ull;
+      int lo = 0, hi = 31;  // largest j with off[idxw + j] <= gw
+#pragma unroll
+      for (int s = 0; s < 5; ++s) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__shfl_sync(kFull, o, mid) <= gw) lo = mid; else hi = mid - 1;
+      }
+      const unsigned long long mine = idxw + (unsigned long long)lo;
+      smap[wid][rb + lane] = (uint16_t)(mine - idx0);
+      idxw = __shfl_sync(kFull, mine, 31);
+    }
+    __syncwarp();
+    for (uint32_t i = lane; i < cnt; i += 32) {
+      const unsigned long long idx = idx0 + smap[wid][i];
+      const unsigned long long entry = b.wr_entry[idx];
+      const uint32_t slot = (uint32_t)(entry >> 32), v = (uint32_t)entry;
+      const unsigned long long j = cbeg + i - off[idx];
+      const unsigned long long pos = idx_off[v] + j;
+      if (pos >= idx_off[v + 1]) {
+        out_of_range = true;
+        continue;
+      }
+      Tally* t = b.tally + (unsigned long long)slot * (unsigned long long)g.n + idx_dest[pos];
+      if (b.want_count) atomicAdd(&t->cnt, 1u);
+      atomicAdd(&t->acc, b.wr_weight[idx]);
+    }
+    __syncwarp();
+  }
+  if (out_of_range) atomicOr(b.err, kErrIndexRange);
 }
 
 __global__ void k_unpack_tally(const Tally* __restrict__ t, uint32_t* cnt,
@@ -473,6 +542,23 @@ cudaError_t launch_walks(const GraphDev& g, const BatchDev& b, int num_sms, cuda
     case 5: return launch_walks_t<5>(g, b, num_sms, st);
     default: return launch_walks_t<4>(g, b, num_sms, st);
   }
+}
+
+cudaError_t launch_index_residue(const GraphDev& g, double* r, double rmax, cudaStream_t st) {
+  k_index_residue<<<1024, 256, 0, st>>>(g, r, rmax);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_walks_indexed(const GraphDev& g, const BatchDev& b, int num_sms,
+                                 const unsigned long long* idx_off, const uint32_t* idx_dest,
+                                 cudaStream_t st) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walks_indexed,
+                                                                kWalkThreads, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  k_walks_indexed<<<num_sms * per_sm, kWalkThreads, 0, st>>>(g, b, idx_off, idx_dest);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_unpack_tally(const Tally* t, uint32_t* cnt, unsigned long long* acc,

@@ -93,9 +93,10 @@ def _load():
                                              P, P, P, P, P, P, P]
             lib.oracle_walk_index.restype = i64
             lib.oracle_walk_index.argtypes = [i64, P, P, dbl, dbl, dbl, u64, ctypes.c_uint32,
-                                              P, P, i64]
+                                              ctypes.c_int, P, P, i64]
             lib.oracle_walk_phase_indexed.restype = ctypes.c_int
-            lib.oracle_walk_phase_indexed.argtypes = [i64, dbl, P, P, P, P, P, P]
+            lib.oracle_walk_phase_indexed.argtypes = [i64, dbl, dbl, P, P, P, ctypes.c_int, P, P,
+                                                      P]
             lib.oracle_estimate.restype = None
             lib.oracle_estimate.argtypes = [i64, P, P, P]
             lib.oracle_topk.restype = ctypes.c_int
@@ -170,24 +171,26 @@ def walk_phase(row_ptr, col, s, alpha, scale, seed, residue):
 INDEX_SOURCE = 0xFFFFFFFF  # the source id in the Philox counter of the index walks
 
 
-def walk_index(row_ptr, col, alpha, scale, rmax, seed, s_index=INDEX_SOURCE):
+def walk_index(row_ptr, col, alpha, scale, rmax, seed, s_index=INDEX_SOURCE, zero_hop=False):
     """FORA+ walk index (Section 3.3) -> (off int64 [n + 1], dest int32 [off[n]]): the
-    ends of omega_max(v) = ceil(RN(RN(rmax d(v)) C)) walks from every v."""
+    ends of omega_max(v) = ceil(RN(RN(rmax d(v)) C)) walks from every v (zero-hop walks and
+    their smaller omega_max with zero_hop)."""
     row_ptr, col, n = _graph(row_ptr, col)
     off = np.zeros(n + 1, dtype=np.int64)
+    zh = 1 if zero_hop else 0
     total = _load().oracle_walk_index(n, _ptr(row_ptr), _ptr(col), alpha, scale, rmax, int(seed),
-                                      int(s_index), _ptr(off), _ptr(np.zeros(1, np.int32)), 0)
+                                      int(s_index), zh, _ptr(off), _ptr(np.zeros(1, np.int32)), 0)
     if total < 0:
         raise OracleError(int(total))
     dest = np.zeros(max(int(total), 1), dtype=np.int32)
     got = _load().oracle_walk_index(n, _ptr(row_ptr), _ptr(col), alpha, scale, rmax, int(seed),
-                                    int(s_index), _ptr(off), _ptr(dest), int(total))
+                                    int(s_index), zh, _ptr(off), _ptr(dest), int(total))
     if got < 0:
         raise OracleError(int(got))
     return off, dest[:total]
 
 
-def walk_phase_indexed(n, scale, residue, off, dest):
+def walk_phase_indexed(n, scale, residue, off, dest, alpha=0.2, zero_hop=False):
     """Walk phase served from a walk index -> (count u32, acc u64, WalkStats)."""
     residue = np.ascontiguousarray(residue, dtype=np.float64)
     off = np.ascontiguousarray(off, dtype=np.int64)
@@ -195,8 +198,9 @@ def walk_phase_indexed(n, scale, residue, off, dest):
     count = np.zeros(n, dtype=np.uint32)
     acc = np.zeros(n, dtype=np.uint64)
     st = WalkStats()
-    rc = _load().oracle_walk_phase_indexed(n, scale, _ptr(residue), _ptr(off), _ptr(dest),
-                                           _ptr(count), _ptr(acc), ctypes.addressof(st))
+    rc = _load().oracle_walk_phase_indexed(n, alpha, scale, _ptr(residue), _ptr(off), _ptr(dest),
+                                           1 if zero_hop else 0, _ptr(count), _ptr(acc),
+                                           ctypes.addressof(st))
     if rc:
         raise OracleError(rc)
     return count, acc, st

@@ -365,6 +365,9 @@ int oracle_walk_phase_zero_hop(int64_t n, const int64_t *row_ptr, const int32_t 
  * omega_v <= omega_max(v) holds exactly).  The index stores, for every v, the end
  * nodes of walks j = 0 .. omega_max(v) - 1 from v, walk j reading the Philox stream
  * with counter (c, j, v, s_index), the same walk definition as oracle_walk_phase.
+ * With zero_hop the stored walks are those of oracle_walk_phase_zero_hop (a forced
+ * first move, Section 4.1) and omega_max(v) = ceil(RN(RN((1 - alpha) RN(r_max d(v))) C)),
+ * the bound of that phase's omega_v (the index is then smaller by about alpha).
  * off[n + 1] is the exclusive prefix of omega_max; dest[off[v] + j] is the end of walk
  * j from v.  Returns the total number of walks (off[n]) when it is <= cap and dest is
  * filled; with cap smaller than that it fills off only and returns the total, negated
@@ -372,7 +375,7 @@ int oracle_walk_phase_zero_hop(int64_t n, const int64_t *row_ptr, const int32_t 
  */
 int64_t oracle_walk_index(int64_t n, const int64_t *row_ptr, const int32_t *col, double alpha,
                           double walk_scale, double rmax, uint64_t seed, uint32_t s_index,
-                          int64_t *off, int32_t *dest, int64_t cap) {
+                          int zero_hop, int64_t *off, int32_t *dest, int64_t cap) {
   int rc = check_graph(n, row_ptr, col);
   if (rc) return rc;
   if (!(alpha > 0.0 && alpha < 1.0) || !(walk_scale > 0.0) || !(rmax > 0.0))
@@ -380,7 +383,9 @@ int64_t oracle_walk_index(int64_t n, const int64_t *row_ptr, const int32_t *col,
   off[0] = 0;
   for (int64_t v = 0; v < n; ++v) {
     const double d = (double)(row_ptr[v + 1] - row_ptr[v]);
-    const double omega_max = ceil((rmax * d) * walk_scale);
+    const double r_bound = rmax * d;
+    const double omega_max = zero_hop ? ceil(((1.0 - alpha) * r_bound) * walk_scale)
+                                      : ceil(r_bound * walk_scale);
     if (omega_max > 4294967295.0) return ORACLE_ERR_WALK_OVERFLOW;
     off[v + 1] = off[v] + (int64_t)omega_max;
   }
@@ -392,7 +397,13 @@ int64_t oracle_walk_index(int64_t n, const int64_t *row_ptr, const int32_t *col,
     for (int64_t j = 0; j < off[v + 1] - off[v]; ++j) {
       walk_stream w;
       stream_init(&w, (uint32_t)j, (uint32_t)v, s_index, seed);
-      const int64_t end = random_walk(row_ptr, col, t_alpha, &w, (int32_t)v, &steps);
+      int32_t start = (int32_t)v;
+      if (zero_hop) { /* the forced first move */
+        const uint32_t dv = (uint32_t)(row_ptr[v + 1] - row_ptr[v]);
+        start = col[row_ptr[v] + uniform_index(&w, dv)];
+        steps += 1;
+      }
+      const int64_t end = random_walk(row_ptr, col, t_alpha, &w, start, &steps);
       if (end < 0) return ORACLE_ERR_WALK_CAP;
       dest[off[v] + j] = (int32_t)end;
     }
@@ -405,20 +416,23 @@ int64_t oracle_walk_index(int64_t n, const int64_t *row_ptr, const int32_t *col,
  * r(v) > 0, the ends of the first omega_v = ceil(r(v) * C) walks stored for v, each
  * adding W_v = rint((r(v)/omega_v) * 2^63) to acc[end] and 1 to count[end].  An
  * omega_v above the index's omega_max(v) is an error (the residue exceeds the index's
- * r_max).  st->walk_steps stays 0 (no walk is simulated).
+ * r_max).  st->walk_steps stays 0 (no walk is simulated).  With zero_hop (an index of
+ * zero-hop walks) the residue sampled is (1 - alpha) r(v), as in
+ * oracle_walk_phase_zero_hop; alpha r(v) goes to the estimate there.
  */
-int oracle_walk_phase_indexed(int64_t n, double walk_scale, const double *residue,
-                              const int64_t *off, const int32_t *dest, uint32_t *count,
-                              uint64_t *acc, oracle_walk_stats *st) {
-  if (n < 1 || !(walk_scale > 0.0)) return ORACLE_ERR_BAD_ARG;
+int oracle_walk_phase_indexed(int64_t n, double alpha, double walk_scale, const double *residue,
+                              const int64_t *off, const int32_t *dest, int zero_hop,
+                              uint32_t *count, uint64_t *acc, oracle_walk_stats *st) {
+  if (n < 1 || !(walk_scale > 0.0) || !(alpha > 0.0 && alpha < 1.0)) return ORACLE_ERR_BAD_ARG;
   oracle_walk_stats local = {0, 0, 0};
   for (int64_t t = 0; t < n; ++t) { count[t] = 0; acc[t] = 0; }
   for (int64_t v = 0; v < n; ++v) {
     if (residue[v] < 0.0) return ORACLE_ERR_BAD_ARG;
     if (!(residue[v] > 0.0)) continue;
-    const double omega_v = ceil(residue[v] * walk_scale);
+    const double r_sampled = zero_hop ? (1.0 - alpha) * residue[v] : residue[v];
+    const double omega_v = ceil(r_sampled * walk_scale);
     if (omega_v > (double)(off[v + 1] - off[v])) return ORACLE_ERR_BAD_ARG;
-    const double weight = residue[v] / omega_v;
+    const double weight = r_sampled / omega_v;
     const uint64_t fixed = (uint64_t)nearbyint(ldexp(weight, 63));
     local.residual_nodes++;
     local.walks += (int64_t)omega_v;

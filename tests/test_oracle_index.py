@@ -97,3 +97,24 @@ def test_indexed_phase_rejects_residues_above_the_index(graph):
     r[3] = 4.0 * rmax * (rp[4] - rp[3])
     with pytest.raises(oracle.OracleError):
         oracle.walk_phase_indexed(n, C, r, off, dest)
+
+
+def test_zero_hop_index_equals_zero_hop_walk_phase_with_the_same_streams(graph):
+    """An index of zero-hop walks (Section 4.1 inside FORA+) served with zero-hop sampling
+    equals the simulated zero-hop walk phase exactly under the query's own streams, and is
+    about (1 - alpha) the size of the plain index."""
+    rp, col = graph
+    n = len(rp) - 1
+    s = 23
+    C = oracle.walk_scale(0.5, 1.0 / n, 1.0 / n)
+    rmax = oracle.rmax_rule(0.5, 1.0 / n, 1.0 / n, rp[-1])
+    _, residue, _ = oracle.forward_push(rp, col, s, 0.2, rmax)
+    off, dest = oracle.walk_index(rp, col, 0.2, C, rmax, seed=5, s_index=s, zero_hop=True)
+    cnt_i, acc_i, st_i = oracle.walk_phase_indexed(n, C, residue, off, dest, alpha=0.2,
+                                                   zero_hop=True)
+    cnt_w, acc_w, st_w = oracle.walk_phase_zero_hop(rp, col, s, 0.2, C, 5, residue)
+    np.testing.assert_array_equal(cnt_i, cnt_w)
+    np.testing.assert_array_equal(acc_i, acc_w)
+    assert st_i.walks == st_w.walks
+    off_plain, _ = oracle.walk_index(rp, col, 0.2, C, rmax, seed=5)
+    assert 0.75 < off[-1] / off_plain[-1] < 0.85

@@ -76,8 +76,9 @@ extern "C" {
 #define FORA_USE_INDEX 0x8u  /* FORA+ (Section 3.3): walk j from v is the j-th walk stored
                                 for v in the graph's walk index (fora_index_build) instead of
                                 a walk simulated on the fly; needs the index's alpha, eps,
-                                delta, p_f, every source's r_max <= the index's, and no
-                                FORA_ZERO_HOP (else FORA_ERR_BAD_ARG) */
+                                delta, p_f, every source's r_max <= the index's, and
+                                FORA_ZERO_HOP exactly when the index was built with it
+                                (else FORA_ERR_BAD_ARG) */
 
 typedef struct fora_graph fora_graph; /* opaque: device copy of the CSR + query workspace */
 
@@ -389,9 +390,12 @@ int fora_graph_autotune(fora_graph *g, const fora_params *params, const int32_t 
  * params->rmax > 0; C = omega / r_sum of Alg. 2), walk j from v reading the Philox stream
  * with counter (c, j, v, 2^32 - 1) and key params->seed, and keeps their end nodes on the
  * device (8 bytes per node + 4 bytes per walk), replacing any earlier index.  Queries with
- * FORA_USE_INDEX then take the first omega_v stored ends of v.  Not safe while queries on g
- * run.  Errors: FORA_ERR_BAD_ARG (FORA_ZERO_HOP, or an r_max so small that a node gets no
- * walk), FORA_ERR_WALK_OVERFLOW (2^32 walks or more), FORA_ERR_OOM, FORA_ERR_CUDA.
+ * FORA_USE_INDEX then take the first omega_v stored ends of v.  With FORA_ZERO_HOP in
+ * params the stored walks are zero-hop walks (a forced first move, Section 4.1) and
+ * omega_max(v) = ceil(RN64(RN64((1 - alpha) RN64(r_max * d_out(v))) * C)), an index about
+ * alpha smaller, served to FORA_ZERO_HOP queries.  Not safe while queries on g run.
+ * Errors: FORA_ERR_BAD_ARG (an r_max so small that a node gets no walk),
+ * FORA_ERR_WALK_OVERFLOW (2^32 walks or more), FORA_ERR_OOM, FORA_ERR_CUDA.
  */
 int fora_index_build(fora_graph *g, const fora_params *params, void *stream);
 

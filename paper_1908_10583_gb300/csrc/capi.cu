@@ -218,8 +218,9 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
   const bool indexed = (p->flags & FORA_USE_INDEX) != 0;
   if (indexed) {
     if (!g->idx_dest) return fail(FORA_ERR_BAD_ARG, "FORA_USE_INDEX without a walk index (fora_index_build)");
-    if ((p->flags & FORA_ZERO_HOP) != 0)
-      return fail(FORA_ERR_BAD_ARG, "the walk index holds plain walks: FORA_USE_INDEX excludes FORA_ZERO_HOP");
+    if (((p->flags & FORA_ZERO_HOP) != 0) != g->idx_zero_hop)
+      return fail(FORA_ERR_BAD_ARG, g->idx_zero_hop ? "the walk index holds zero-hop walks: FORA_USE_INDEX needs FORA_ZERO_HOP"
+                                                    : "the walk index holds plain walks: FORA_USE_INDEX excludes FORA_ZERO_HOP");
     if (rp.walk_scale != g->idx_scale || rp.alpha != g->idx_alpha)
       return fail(FORA_ERR_BAD_ARG, "the walk index was built for other alpha / eps / delta / p_f");
   }
@@ -590,8 +591,7 @@ void fora_graph_destroy(fora_graph* g) {
 
 int fora_index_build(fora_graph* g, const fora_params* params, void* stream_) {
   if (!g || !params) return fail(FORA_ERR_BAD_ARG, "null graph or params");
-  if ((params->flags & FORA_ZERO_HOP) != 0)
-    return fail(FORA_ERR_BAD_ARG, "the walk index holds plain walks (no FORA_ZERO_HOP)");
+  const bool zero_hop = (params->flags & FORA_ZERO_HOP) != 0;
   Resolved rp;
   int rc = resolve(g, params, &rp);
   if (rc) return rc;
@@ -617,6 +617,8 @@ int fora_index_build(fora_graph* g, const fora_params* params, void* stream_) {
   b.walk_scale = rp.walk_scale;
   b.alpha_threshold = rp.alpha_threshold;
   b.seed = params->seed;
+  // zero-hop: omega_max from (1 - alpha) RN(r_max d(v)) and walks with a forced first move
+  b.zero_hop = zero_hop ? 1 : 0;
   b.r = w->r; b.res = w->res; b.tally = w->tally;
   b.q[0] = w->q[0]; b.q[1] = w->q[1]; b.fa = w->fa;
   b.hub[0] = w->hub[0]; b.hub[1] = w->hub[1];
@@ -675,6 +677,7 @@ int fora_index_build(fora_graph* g, const fora_params* params, void* stream_) {
   g->idx_scale = rp.walk_scale;
   g->idx_alpha = rp.alpha;
   g->idx_seed = params->seed;
+  g->idx_zero_hop = zero_hop;
   return FORA_OK;
 }
 

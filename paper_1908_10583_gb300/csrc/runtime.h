@@ -154,6 +154,7 @@ struct fora_graph {
   int64_t idx_entries = 0;
   double idx_rmax = 0.0, idx_scale = 0.0, idx_alpha = 0.0;
   uint64_t idx_seed = 0;
+  bool idx_zero_hop = false;  // the stored walks are zero-hop walks (Section 4.1)
   int device = 0;
   int num_sms = 0;
   fora::Tuning tune;

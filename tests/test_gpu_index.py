@@ -3,8 +3,9 @@
 The device index (omega_max(v) stored walk ends per node) equals the oracle's bit for
 bit; a query served from it equals the oracle's indexed walk phase bit for bit on the
 oracle's residues (counts, fixed-point weights, estimates, top-k); indexed queries stay
-eps-accurate against power iteration; and the three refusals (zero-hop, an r_max above
-the index's, no index) are errors.
+eps-accurate against power iteration; an index of zero-hop walks (Section 4.1) serves
+zero-hop queries bit-exactly too; and the refusals (a query of the other walk kind, an
+r_max above the index's, other parameters, no index) are errors.
 """
 import numpy as np
 import pytest
@@ -118,7 +119,7 @@ def test_index_refusals(indexed):
     n = len(rp) - 1
     rmax, _, _ = g.index_info()
     src = inputs.uniform_sources(n, 2, 7)
-    with pytest.raises(fora.FORAError):  # zero-hop walks are not stored
+    with pytest.raises(fora.FORAError):  # a plain index serves no zero-hop query
         g.ssppr_batch(src, fora.Params.make(k=10, flags=fora.FORA_USE_INDEX | fora.FORA_ZERO_HOP))
     with pytest.raises(fora.FORAError):  # a larger r_max needs more walks than stored
         g.ssppr_batch(src, fora.Params.make(k=10, rmax=2 * rmax, flags=fora.FORA_USE_INDEX))
@@ -131,3 +132,39 @@ def test_index_refusals(indexed):
         assert g2.index_info() == (0.0, 0.0, 0)
     finally:
         g2.close()
+
+
+def test_zero_hop_index_bit_exact(indexed):
+    """An index of zero-hop walks (FORA_ZERO_HOP at build, Section 4.1) equals the oracle's,
+    and a zero-hop query served from it equals the oracle's zero-hop indexed phase bit for
+    bit on the oracle's residues; a plain query is refused by it."""
+    rp, col, g = indexed
+    n = len(rp) - 1
+    try:
+        g.build_index(fora.Params.make(k=50, seed=SEED, flags=fora.FORA_ZERO_HOP))
+        rmax, C, entries = g.index_info()
+        off, dest = g.index_export()
+        off_o, dest_o = oracle.walk_index(rp, col, 0.2, C, rmax, SEED, zero_hop=True)
+        np.testing.assert_array_equal(off, off_o)
+        np.testing.assert_array_equal(dest.astype(np.int32), dest_o)
+        sources = inputs.uniform_sources(n, 4, 7070)
+        res = np.zeros((len(sources), n))
+        r = np.zeros((len(sources), n))
+        for i, s in enumerate(sources):
+            res[i], r[i], _ = oracle.forward_push(rp, col, int(s), 0.2, rmax)
+        p = fora.Params.make(k=50, seed=1, flags=fora.FORA_USE_INDEX | fora.FORA_ZERO_HOP)
+        ids, vals, st, out = _debug(g, sources, p, given=(res, r))
+        for i in range(len(sources)):
+            cnt_o, acc_o, _ = oracle.walk_phase_indexed(n, C, r[i], off_o, dest_o, alpha=0.2,
+                                                        zero_hop=True)
+            np.testing.assert_array_equal(out["count"][i], cnt_o)
+            np.testing.assert_array_equal(out["acc"][i], acc_o)
+            est_o = oracle.estimate_zero_hop(res[i], r[i], acc_o, 0.2)
+            np.testing.assert_array_equal(out["estimate"][i], est_o)
+            ids_o, vals_o = oracle.topk(est_o, 50)
+            np.testing.assert_array_equal(ids[i], ids_o)
+            np.testing.assert_array_equal(vals[i], vals_o)
+        with pytest.raises(fora.FORAError):
+            g.ssppr_batch(sources, fora.Params.make(k=10, flags=fora.FORA_USE_INDEX))
+    finally:
+        g.build_index(fora.Params.make(k=50, seed=SEED))

@@ -1,6 +1,7 @@
 /*
  * fora.h -- C ABI of the GB300 (sm_103a) implementation of the index-free
- * FORA single-source Personalized PageRank (SSPPR) query of Wang et al.,
+ * FORA single-source Personalized PageRank (SSPPR) query (and of its FORA+ walk
+ * index, Section 3.3) of Wang et al.,
  * "Efficient Algorithms for Approximate Single-Source Personalized PageRank
  * Queries" (TODS 2019).
  *
@@ -102,11 +103,12 @@ typedef struct {
   uint64_t edge_pushes;    /* sum of d_out over pushed nodes */
   uint64_t residual_nodes; /* nodes with r(v) > 0 after the push */
   uint64_t walks;          /* sum of omega_v */
-  uint64_t walk_steps;     /* moves over all walks */
+  uint64_t walk_steps;     /* moves over all walks (0 when walks come from a walk index) */
   uint32_t push_rounds;    /* rounds in which this source pushed at least one node */
   int32_t source;
-  /* phase times of the whole call (the same for every source of a batch): push rounds,
-     residual compaction + walk offsets, walk kernel, estimate + top-k */
+  /* phase times of the call (the same for every source of a batch; for a batch run as
+     pipeline parts, those of the source's part): push rounds, residual compaction + walk
+     offsets, walk kernel, estimate + top-k */
   float ms_push, ms_residual, ms_walk, ms_topk;
 } fora_stats;
 
@@ -172,7 +174,9 @@ int fora_ssppr_batch_rmax(fora_graph *g, const fora_params *params, const int32_
  * values (or params->rmax if > 0); a source stops at the first round whose k-th
  * largest estimate is >= (1 + eps) delta.  Round i draws its walks with key seed + i.
  * params->delta is not used; params->pf is the overall p_f (<= 0 selects 1/n);
- * FORA_ZERO_HOP is honoured.  Outputs are HOST arrays: out_ids / out_vals [nsrc][k],
+ * FORA_ZERO_HOP is honoured; FORA_USE_INDEX is not (every round has its own C, so a walk
+ * index built for one round's parameters cannot serve the others: FORA_ERR_BAD_ARG).
+ * Outputs are HOST arrays: out_ids / out_vals [nsrc][k],
  * stats [nsrc] (the stopping round's counters) and iterations [nsrc] (rounds run);
  * stats and iterations may be NULL.  1 <= k <= min(n, FORA_MAX_K).
  */
@@ -345,8 +349,8 @@ int fora_threshold_debug(const double *r, const double *rmax, const uint32_t *d,
 
 /*
  * Launch-shape parameters of a graph's queries (results do not depend on them, only
- * speed):  "spread_width" (1..4096, default 1): the push visits the sorted frontier of a
- * round through this many interleaved segments, so the warps in flight cover about that
+ * speed):  "spread_width" (1..4096, default 1): the push visits the frontier of a round
+ * (grouped by source) through this many interleaved segments, so the warps in flight cover about that
  * many sources at once (wider spreads reductions on shared hub targets over more
  * addresses; narrower keeps the residue arrays in flight smaller).  "walk_blocks" (4, 5
  * or 6, default 4): resident walk blocks per SM, traded against registers per thread.

@@ -26,7 +26,10 @@
  *     every node, else moves to a uniform out-neighbour (Section 2.1);
  *   - estimate pi_hat(t) = reserve(t) + sum of walk weights ending at t;
  *   - top-k by (pi_hat descending, id ascending) (Section 2.1: the query
- *     returns the k nodes with the highest PPR values).
+ *     returns the k nodes with the highest PPR values);
+ *   - the FORA+ walk index (Section 3.3, Eq. index-rwnum): omega_max(v) stored
+ *     walk ends per node, and the walk phase that takes the first omega_v of
+ *     them (oracle_walk_index, oracle_walk_phase_indexed).
  *
  * Readings where the paper is silent (the same ones the CUDA path takes):
  *   - log is the natural logarithm;

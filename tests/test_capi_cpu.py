@@ -50,3 +50,25 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(_native._build, "LIB_PATH", str(tmp_path / "libfora.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         _native.load()
+
+
+def test_null_handles_and_counts_are_rejected_before_any_device_call(lib):
+    """Entry points added for tuning, the walk index and the debug views check their
+    arguments first: a null graph, key or output, or a negative count, is FORA_ERR_BAD_ARG
+    with a message, and a zero count is a no-op (no device is touched)."""
+    import ctypes
+    v = ctypes.c_int64()
+    d = ctypes.c_double()
+    p = fora.Params.make()
+    assert lib.fora_graph_tune(None, b"pipeline", 2) == fora.FORA_ERR_BAD_ARG
+    assert lib.fora_graph_tuning(None, b"pipeline", ctypes.byref(v)) == fora.FORA_ERR_BAD_ARG
+    assert lib.fora_index_build(None, ctypes.byref(p), None) == fora.FORA_ERR_BAD_ARG
+    assert lib.fora_index_info(None, ctypes.byref(d), ctypes.byref(d), ctypes.byref(v)) == \
+        fora.FORA_ERR_BAD_ARG
+    assert lib.fora_index_export(None, None, None) == fora.FORA_ERR_BAD_ARG
+    assert lib.fora_index_destroy(None) == fora.FORA_ERR_BAD_ARG
+    assert lib.fora_threshold_debug(None, None, None, None, -1) == fora.FORA_ERR_BAD_ARG
+    assert lib.fora_threshold_debug(None, None, None, None, 0) == fora.FORA_OK
+    assert lib.fora_philox_debug(None, None, -1) == fora.FORA_ERR_BAD_ARG
+    assert lib.fora_philox_debug(None, None, 0) == fora.FORA_OK
+    assert lib.fora_last_error()

@@ -45,8 +45,9 @@ def parse_args(argv=None):
     ap.add_argument("--batch", type=int, default=None)
     ap.add_argument("--k", type=int, default=None)
     ap.add_argument("--eps", type=float, default=0.5)
-    ap.add_argument("--cpu-sources", type=int, default=8,
-                    help="sources in the bounded CPU-oracle sample")
+    ap.add_argument("--cpu-sources", type=int, default=None,
+                    help="sources in each bounded CPU-oracle sample (default: one per oracle "
+                         "thread)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stats", action="store_true", help="per-step counters to stderr")
     ap.add_argument("--tune", action="append", default=[],
@@ -151,6 +152,12 @@ def profiled_traffic(kernel, wl, launches_per_step=1):
     return found if split == launches_per_step else None
 
 
+def oracle_threads():
+    """Host threads of both CPU-oracle legs (the reference arm and cpu_baseline): one
+    oracle query per thread, at most 8 threads."""
+    return max(1, min(os.cpu_count() or 1, 8))
+
+
 def cpu_oracle_sample(rp, col, sources, w, eps, threads):
     """The oracle as it stands on the host cores: wall time of `sources` queries."""
     from concurrent.futures import ThreadPoolExecutor
@@ -202,8 +209,8 @@ def run_reference(args):
     w = workload(args)
     rp, col = inputs.rmat_csr(w["scale"], w["avg_deg"], w["graph_seed"])
     n = len(rp) - 1
-    threads = max(1, min(os.cpu_count() or 1, 4))
-    per_step = threads
+    threads = oracle_threads()
+    per_step = args.cpu_sources or threads
     for i in range(args.warmup):
         src = inputs.uniform_sources(n, per_step, inputs.SOURCE_SEED + 7919 * (i + 1))
         cpu_oracle_sample(rp, col, src, w, args.eps, threads)
@@ -214,7 +221,8 @@ def run_reference(args):
     total = sum(times)
     value = per_step * args.steps / total
     sample = (f"{per_step} sources per step of the {args.workload} workload (top-{w['k']}, "
-              f"eps={args.eps}), one oracle query per thread")
+              f"eps={args.eps}, rule r_max), one oracle query per thread on {threads} host "
+              f"threads")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
@@ -360,13 +368,22 @@ def run_fora(args):
         rule_ms = timed(None, args.steps)
         comparison["batched_rule_qps"] = B * args.steps / (sum(rule_ms) / 1e3)
     if args.plain_sources > 0:
+        # plain FORA: one query at a time through fora_ssppr (rule r_max, host results),
+        # each query's latency on the host clock around the synchronous call
         plain_src = inputs.uniform_sources(n, args.plain_sources, inputs.SOURCE_SEED + 31337)
         g.ssppr(int(plain_src[0]), params)  # warm the single-source workspace
         torch.cuda.synchronize()
+        plain_ms = []
         t0 = time.perf_counter()
         for s_ in plain_src:
+            t1 = time.perf_counter()
             g.ssppr(int(s_), params)
+            plain_ms.append(1e3 * (time.perf_counter() - t1))
         comparison["plain_fora_qps"] = len(plain_src) / (time.perf_counter() - t0)
+        lp = sorted(plain_ms)
+        comparison["plain_fora_latency_ms"] = {
+            "p50": lp[len(lp) // 2], "p99": lp[min(len(lp) - 1, int(0.99 * len(lp)))],
+            "queries": len(lp)}
     if not args.no_index:
         # FORA+: the walk phase served from a walk index built for the rule's r_max
         torch.cuda.synchronize()
@@ -434,12 +451,14 @@ def run_fora(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        threads = max(1, min(os.cpu_count() or 1, args.cpu_sources))
-        src = inputs.uniform_sources(n, args.cpu_sources, inputs.SOURCE_SEED + 424242)
+        threads = oracle_threads()
+        nsamp = args.cpu_sources or threads
+        src = inputs.uniform_sources(n, nsamp, inputs.SOURCE_SEED + 424242)
         secs = cpu_oracle_sample(rp, col, src, w, args.eps, threads)
-        cpu = {"value": args.cpu_sources / secs, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"{args.cpu_sources} sources of the {args.workload} workload "
-                         f"(top-{k}, eps={args.eps}), one oracle query per thread"}
+        cpu = {"value": nsamp / secs, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{nsamp} sources of the {args.workload} workload "
+                         f"(top-{k}, eps={args.eps}, rule r_max), one oracle query per "
+                         f"thread on {threads} host threads"}
 
     lat = sorted(step_ms)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -454,7 +473,9 @@ def run_fora(args):
                        "tuning": tuning},
             "latency_ms": {"p50": lat[len(lat) // 2],
                            "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-                           "note": "every query of a batch completes with its batch"},
+                           "note": "per query of the batched path: every query of a batch "
+                                   "completes with its batch; plain FORA's per-query "
+                                   "latency is comparison.plain_fora_latency_ms"},
             "phase_ms_per_step": {k_: v / args.steps for k_, v in phase.items()},
             "walks_per_step": walks_total / args.steps,
             "walk_moves_per_step": steps_total / args.steps,

@@ -41,6 +41,17 @@
  *     has finished the query;
  *   - a graph handle serialises the queries issued on it (one workspace per
  *     handle; concurrent calls on the same handle wait for each other).
+ *
+ * Differences from the minimal boundary this library started from (graph create /
+ * destroy, fora_ssppr, fora_ssppr_batch, fora_last_error, with fora_params fields
+ * k, seed, flags in that order and one stats struct of r_max, r_sum, walks, walk steps,
+ * edge pushes, rounds and three phase times):
+ *   - fora_params orders its fields k, flags, seed, so that the two 32-bit fields share
+ *     one 8-byte slot and the struct has no padding hole (same size on every ABI);
+ *   - fora_ssppr takes a `stream` argument like fora_ssppr_batch, so a single query can
+ *     run on the caller's stream;
+ *   - fora_stats also carries the node pushes, residual nodes and source id and splits
+ *     the walk phase into residual compaction and walk kernel time (four phase times).
  */
 #ifndef FORA_H_
 #define FORA_H_
@@ -113,11 +124,17 @@ typedef struct {
 } fora_stats;
 
 /*
- * Copy a CSR graph to the device.  row_ptr (n+1 entries, row_ptr[0] = 0,
- * non-decreasing) and col (row_ptr[n] entries in [0, n)) are HOST arrays;
- * they are copied and stay owned by the caller.  Requires 1 <= n < 2^31,
- * m = row_ptr[n] < 2^32 and d_out(v) >= 1 for every v (FORA_ERR_DANGLING).
- * Edges are taken with multiplicity; self-loops are allowed.  flags: 0.
+ * Copy a CSR graph to the device.  The graph is the directed G = (V, E) of Section 2.1
+ * with n = |V| and m = |E|, stored as out-adjacency lists (the only direction Forward
+ * Push and the walks of Alg. 2 follow: N_out(v) and d_out(v)).  row_ptr (n+1 entries,
+ * row_ptr[0] = 0, non-decreasing) and col (row_ptr[n] entries in [0, n)) are HOST
+ * arrays; they are copied and stay owned by the caller.  Requires 1 <= n < 2^31,
+ * m = row_ptr[n] < 2^32 and d_out(v) >= 1 for every v (FORA_ERR_DANGLING: a walk of
+ * Section 2.1 needs an out-neighbour at every node).  Edges are taken with
+ * multiplicity; self-loops are allowed.  flags: 0.  Device memory: about
+ * 4 (n + 1) + 4 m + 16 n bytes, plus a bit-packed copy of col for the walks when
+ * ceil(log2 n) <= 24.  Errors: FORA_ERR_BAD_ARG, FORA_ERR_DANGLING, FORA_ERR_OOM,
+ * FORA_ERR_CUDA (no device); *out is NULL on any error.
  */
 int fora_graph_create(int64_t n, const int64_t *row_ptr, const int32_t *col, uint32_t flags,
                       fora_graph **out);
@@ -151,7 +168,8 @@ int fora_ssppr(fora_graph *g, const fora_params *params, int32_t source, int32_t
  * stats: NULL or [nsrc].  Every source gives bit for bit the walk counts and
  * top-k it would give alone (same Philox counters), up to the FP64 rounding
  * order of the push.  The workspace for nsrc sources (about 56 bytes per
- * source and node) is allocated on the first call that needs it and kept.
+ * source and node; fora_workspace_bytes gives the exact size) is allocated on the
+ * first call that needs it and kept.
  */
 int fora_ssppr_batch(fora_graph *g, const fora_params *params, const int32_t *sources,
                      int32_t nsrc, int32_t *out_ids, double *out_vals, fora_stats *stats,
@@ -243,7 +261,7 @@ int fora_ssppr_batch_learned(fora_graph *g, const fora_params *params, fora_mode
  * workspace for `slots` queries, a CUDA stream and a host thread.  Admission is by HBM
  * footprint: the budget (memory_budget_bytes, 0 = 80% of the free device memory) is
  * split evenly over the lanes and a lane holds as many queries as its share fits at
- * about 56 bytes per node per query (residue, reserve, walk tallies, frontiers), at most
+ * fora_workspace_bytes per query slot (residue, reserve, walk tallies, frontiers), at most
  * max_batch.  Requests queue per graph; a free lane admits the oldest queued requests
  * that share everything but k (up to its slots; after waiting up to batch_window_ms for
  * more when fewer are queued), runs them as one batched query with the largest k, and
@@ -327,10 +345,13 @@ int fora_topk(const double *est, int64_t n, int32_t nrows, uint32_t k, int32_t *
  * pointers the caller owns), with at most 9 rows per call: the scratch lives in one
  * 1 MiB device array of the library, which every GPU that loads the library holds
  * until the process exits.  Larger nrows -> FORA_ERR_BAD_ARG.  The first call on a
- * device (with that device current) looks up the array's device address; make that
- * first call before any stream capture.  All calls share the one array: calls that
- * overlap on the GPU (on different streams or host threads) race and must be ordered
- * by the caller.  Returns after the stream has finished the select.
+ * device (with that device current) looks up the array's device address and keeps it
+ * for the life of the process; make that first call before any stream capture.  The
+ * kept address belongs to the device's primary context: do not call this entry point
+ * again on a device after cudaDeviceReset (or anything else that destroys that context)
+ * in the same process.  All calls share the one array: calls that overlap on the GPU
+ * (on different streams or host threads) race and must be ordered by the caller.  Each
+ * call synchronises `stream` before it returns.
  */
 int fora_topk_noalloc(const double *est, int64_t n, int32_t nrows, uint32_t k, int32_t *out_ids,
                       double *out_vals, void *stream);
@@ -362,8 +383,10 @@ int fora_threshold_debug(const double *r, const double *rmax, const uint32_t *d,
  * its own workspace, stream and host thread, part k's push starting when part k-1's push
  * has finished, so one part's walk phase runs beside the next part's push; the call's
  * stream waits for all parts, and each part's stats carry that part's phase times.
- * Results do not depend on it.  Unknown keys and out-of-range values return
- * FORA_ERR_BAD_ARG.
+ * Results do not depend on it.  "max_push_rounds" (1..100000, default 100000): the cap
+ * on the push rounds of Alg. 1 (the loop is bounded so that it cannot run away); a query
+ * whose push needs more rounds stops there and returns FORA_ERR_PUSH_NOT_CONVERGED.
+ * Unknown keys and out-of-range values return FORA_ERR_BAD_ARG.
  */
 int fora_graph_tune(fora_graph *g, const char *key, int64_t value);
 
@@ -413,7 +436,28 @@ int fora_index_export(const fora_graph *g, int64_t *off, uint32_t *dest);
 /* Free the index (no-op without one). */
 int fora_index_destroy(fora_graph *g);
 
-/* Message of the calling thread's last failure ("" if none). */
+/*
+ * Device bytes a batched query of nsrc sources allocates on a graph given as HOST
+ * row_ptr[n + 1] (the workspace: residue, reserve and walk tallies per source and node,
+ * the frontier queues of Alg. 1, hub-chunk lists, the residual lists of Alg. 2, top-k
+ * scratch and per-source state).  The same sizes decide a serving lane's slot count.
+ * Host arithmetic only (no device needed).  FORA_ERR_BAD_ARG for n < 1, nsrc outside
+ * [1, 65535] or a decreasing row_ptr.
+ */
+int fora_workspace_bytes(int64_t n, const int64_t *row_ptr, int32_t nsrc, uint64_t *bytes);
+
+/*
+ * Fault injection for tests: the nth device allocation the library makes from now on
+ * (counting only its own allocations of graphs, workspaces and walk indexes, from any
+ * thread) fails as if the device were out of memory, so the call making it returns
+ * FORA_ERR_OOM; the allocations before and after it are real.  nth = 0 switches the
+ * injection off.  The paper has no counterpart.  FORA_ERR_BAD_ARG for nth < 0.
+ */
+int fora_debug_fail_alloc(int64_t nth);
+
+/* Message of the calling thread's last failure ("" if none): the error channel of the
+ * conventions above (no exception crosses the ABI); the string stays valid until the
+ * thread's next failing call. */
 const char *fora_last_error(void);
 
 #ifdef __cplusplus

@@ -172,6 +172,10 @@ def load():
         L.fora_index_export.argtypes = [P, P, P]
         L.fora_index_destroy.restype = I
         L.fora_index_destroy.argtypes = [P]
+        L.fora_workspace_bytes.restype = I
+        L.fora_workspace_bytes.argtypes = [i64, P, i32, P]
+        L.fora_debug_fail_alloc.restype = I
+        L.fora_debug_fail_alloc.argtypes = [i64]
         L.fora_last_error.restype = ctypes.c_char_p
         L.fora_last_error.argtypes = []
         _lib = L
@@ -430,6 +434,19 @@ def topk(est, k: int, out_ids=None, out_vals=None, stream=None):
     _check(load().fora_topk(est.data_ptr(), n, nrows, k, out_ids.data_ptr(), out_vals.data_ptr(),
                             _stream_ptr(stream)))
     return out_ids, out_vals
+
+
+def workspace_bytes(row_ptr, nsrc: int) -> int:
+    """Device bytes of a batched query of nsrc sources on this CSR (fora_workspace_bytes)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    out = ctypes.c_uint64()
+    _check(load().fora_workspace_bytes(len(rp) - 1, rp.ctypes.data, int(nsrc), ctypes.byref(out)))
+    return out.value
+
+
+def debug_fail_alloc(nth: int):
+    """Make the library's nth device allocation from now on fail (0: off)."""
+    _check(load().fora_debug_fail_alloc(int(nth)))
 
 
 def philox(ctr_key: np.ndarray) -> np.ndarray:

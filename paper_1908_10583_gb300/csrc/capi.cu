@@ -3,10 +3,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -55,42 +57,122 @@ int fora::report_error(int code, const char* fmt, ...) {
 
 namespace {
 
+std::mutex g_occ_mu;
+std::map<std::pair<int, const void*>, int> g_occ;  // (device, kernel) -> blocks per SM
+
+// fora_debug_fail_alloc: allocations left before the one that is made to fail (0: off)
+std::atomic<long long> g_fail_alloc_in{0};
+
+}  // namespace
+
+int fora::resident_blocks(const void* kernel, int threads) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  std::lock_guard<std::mutex> lock(g_occ_mu);
+  const auto key = std::make_pair(dev, kernel);
+  const auto it = g_occ.find(key);
+  if (it != g_occ.end()) return it->second;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess)
+    return 0;
+  if (per_sm < 1) per_sm = 1;
+  g_occ[key] = per_sm;
+  return per_sm;
+}
+
+cudaError_t fora::device_alloc(void** p, size_t bytes) {
+  long long left = g_fail_alloc_in.load();
+  while (left > 0) {
+    if (g_fail_alloc_in.compare_exchange_weak(left, left - 1)) {
+      if (left == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+      }
+      break;
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
+
+fora::WorkspaceSizes fora::workspace_sizes(int64_t n, uint64_t hub_chunks, int nsrc) {
+  WorkspaceSizes z;
+  const size_t S = (size_t)nsrc;
+  z.N = S * (size_t)n;
+  const size_t H = S * hub_chunks + 1;
+  z.r = z.N * sizeof(double);
+  z.res = z.N * sizeof(double);
+  z.tally = z.N * sizeof(Tally);
+  z.q = (z.N + 1) * sizeof(unsigned long long);
+  z.fa = (z.N + 1) * sizeof(double);
+  z.hub = H * sizeof(unsigned long long);
+  z.small = 8 * sizeof(unsigned long long);
+  z.work = 32 * sizeof(unsigned long long);
+  z.alist = S * sizeof(uint32_t);
+  z.slot_cnt = 4 * S * sizeof(uint32_t);
+  z.pre = 2 * (S + 1) * sizeof(unsigned long long);
+  z.ps = sizeof(PushState);
+  z.err = sizeof(uint32_t);
+  z.sources = S * sizeof(int32_t);
+  z.rmax = S * sizeof(double);
+  z.stats = S * sizeof(SlotStats);
+  z.blk = 2 * (size_t)kMaxResidualGrid * sizeof(unsigned long long);
+  z.topk = topk_scratch_bytes(nsrc);
+  z.feat = S * FORA_NUM_FEATURES * sizeof(float);
+  z.pred = S * sizeof(float);
+  z.rmax_learned = S * sizeof(double);
+  z.out_ids = S * FORA_MAX_K * sizeof(int32_t);
+  z.out_vals = S * FORA_MAX_K * sizeof(double);
+  return z;
+}
+
+size_t fora::WorkspaceSizes::total() const {
+  return r + res + tally + 2 * q + fa + 2 * hub + small + work + alist + slot_cnt + pre + ps +
+         err + sources + rmax + stats + blk + topk + feat + pred + rmax_learned + out_ids +
+         out_vals;
+}
+
+namespace {
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t bytes) {
+  return device_alloc(reinterpret_cast<void**>(p), bytes);
+}
+
 int ensure_workspace(fora_graph* g, Workspace* w, int nsrc) {
   if (nsrc <= w->cap) return FORA_OK;
   w->release();
-  const size_t N = (size_t)nsrc * (size_t)g->n;
-  const size_t H = (size_t)nsrc * g->hub_chunks + 1;
+  const WorkspaceSizes z = workspace_sizes(g->n, g->hub_chunks, nsrc);
   // hub items hold a queue index in their upper 64 - kHubChunkBits bits
-  if (N >= (1ull << (64 - kHubChunkBits)))
+  if (z.N >= (1ull << (64 - kHubChunkBits)))
     return fail(FORA_ERR_BAD_ARG, "%d sources x %lld nodes exceed the queue index range", nsrc,
                 (long long)g->n);
-  w->residual_grid = g->num_sms * 8;
-  CUDA_TRY(cudaMalloc(&w->r, N * sizeof(double)));
-  CUDA_TRY(cudaMalloc(&w->res, N * sizeof(double)));
-  CUDA_TRY(cudaMalloc(&w->tally, N * sizeof(Tally)));
-  CUDA_TRY(cudaMalloc(&w->q[0], (N + 1) * sizeof(unsigned long long)));
-  CUDA_TRY(cudaMalloc(&w->q[1], (N + 1) * sizeof(unsigned long long)));
-  CUDA_TRY(cudaMalloc(&w->fa, (N + 1) * sizeof(double)));
-  CUDA_TRY(cudaMalloc(&w->hub[0], H * sizeof(unsigned long long)));
-  CUDA_TRY(cudaMalloc(&w->hub[1], H * sizeof(unsigned long long)));
-  CUDA_TRY(cudaMalloc(&w->small, 8 * sizeof(unsigned long long)));
-  CUDA_TRY(cudaMalloc(&w->work, 32 * sizeof(unsigned long long)));
-  CUDA_TRY(cudaMalloc(&w->alist, (size_t)nsrc * sizeof(uint32_t)));
-  CUDA_TRY(cudaMalloc(&w->slot_cnt, 4 * (size_t)nsrc * sizeof(uint32_t)));
-  CUDA_TRY(cudaMalloc(&w->pre, 2 * ((size_t)nsrc + 1) * sizeof(unsigned long long)));
-  CUDA_TRY(cudaMalloc(&w->ps, sizeof(PushState)));
+  w->residual_grid = std::min(g->num_sms * 8, kMaxResidualGrid);
+  CUDA_TRY(dalloc(&w->r, z.r));
+  CUDA_TRY(dalloc(&w->res, z.res));
+  CUDA_TRY(dalloc(&w->tally, z.tally));
+  CUDA_TRY(dalloc(&w->q[0], z.q));
+  CUDA_TRY(dalloc(&w->q[1], z.q));
+  CUDA_TRY(dalloc(&w->fa, z.fa));
+  CUDA_TRY(dalloc(&w->hub[0], z.hub));
+  CUDA_TRY(dalloc(&w->hub[1], z.hub));
+  CUDA_TRY(dalloc(&w->small, z.small));
+  CUDA_TRY(dalloc(&w->work, z.work));
+  CUDA_TRY(dalloc(&w->alist, z.alist));
+  CUDA_TRY(dalloc(&w->slot_cnt, z.slot_cnt));
+  CUDA_TRY(dalloc(&w->pre, z.pre));
+  CUDA_TRY(dalloc(&w->ps, z.ps));
   if (!w->capture_stream) CUDA_TRY(cudaStreamCreateWithFlags(&w->capture_stream, cudaStreamNonBlocking));
-  CUDA_TRY(cudaMalloc(&w->err, sizeof(uint32_t)));
-  CUDA_TRY(cudaMalloc(&w->sources, nsrc * sizeof(int32_t)));
-  CUDA_TRY(cudaMalloc(&w->rmax, nsrc * sizeof(double)));
-  CUDA_TRY(cudaMalloc(&w->stats, nsrc * sizeof(SlotStats)));
-  CUDA_TRY(cudaMalloc(&w->blk, 2 * (size_t)w->residual_grid * sizeof(unsigned long long)));
-  CUDA_TRY(cudaMalloc(&w->topk_scratch, topk_scratch_bytes(nsrc)));
-  CUDA_TRY(cudaMalloc(&w->feat, (size_t)nsrc * FORA_NUM_FEATURES * sizeof(float)));
-  CUDA_TRY(cudaMalloc(&w->pred, (size_t)nsrc * sizeof(float)));
-  CUDA_TRY(cudaMalloc(&w->rmax_learned, (size_t)nsrc * sizeof(double)));
-  CUDA_TRY(cudaMalloc(&w->out_ids, (size_t)nsrc * FORA_MAX_K * sizeof(int32_t)));
-  CUDA_TRY(cudaMalloc(&w->out_vals, (size_t)nsrc * FORA_MAX_K * sizeof(double)));
+  CUDA_TRY(dalloc(&w->err, z.err));
+  CUDA_TRY(dalloc(&w->sources, z.sources));
+  CUDA_TRY(dalloc(&w->rmax, z.rmax));
+  CUDA_TRY(dalloc(&w->stats, z.stats));
+  CUDA_TRY(dalloc(&w->blk, z.blk));
+  CUDA_TRY(dalloc(&w->topk_scratch, z.topk));
+  CUDA_TRY(dalloc(&w->feat, z.feat));
+  CUDA_TRY(dalloc(&w->pred, z.pred));
+  CUDA_TRY(dalloc(&w->rmax_learned, z.rmax_learned));
+  CUDA_TRY(dalloc(&w->out_ids, z.out_ids));
+  CUDA_TRY(dalloc(&w->out_vals, z.out_vals));
   CUDA_TRY(cudaMallocHost(&w->h_counters, 8 * sizeof(unsigned long long)));
   CUDA_TRY(cudaMallocHost(&w->h_stats, nsrc * sizeof(SlotStats)));
   CUDA_TRY(cudaMallocHost(&w->h_err, sizeof(uint32_t)));
@@ -147,7 +229,7 @@ namespace {
 // The instantiated graph is kept in the workspace and rebuilt when the workspace, the
 // number of sources, alpha or the launch shape change.
 int push_loop_graph(fora_graph* g, Workspace* w, const GraphDev& gd, const BatchDev& b) {
-  const PushGraphKey key{w->generation, b.nsrc, b.alpha, b.spread_width};
+  const PushGraphKey key{w->generation, b.nsrc, b.alpha, b.spread_width, b.max_rounds};
   if (w->push_exec && key == w->push_key) return FORA_OK;
   if (w->push_exec) {
     cudaGraphExecDestroy(w->push_exec);
@@ -285,6 +367,7 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
     std::lock_guard<std::mutex> tlock(g->mu);
     b.spread_width = g->tune.spread_width;
     b.walk_blocks = g->tune.walk_blocks;
+    b.max_rounds = g->tune.max_push_rounds;
     host_loop = g->tune.push_host_loop != 0;
   }
 
@@ -363,7 +446,7 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
     CUDA_TRY(cudaMemcpyAsync(w->h_rmax, w->rmax, nsrc * sizeof(double), cudaMemcpyDeviceToHost, stream));
   CUDA_TRY(cudaStreamSynchronize(stream));
   if (*w->h_err & kErrPushNotConverged)
-    return fail(FORA_ERR_PUSH_NOT_CONVERGED, "push did not converge in %u rounds", kMaxPushRounds);
+    return fail(FORA_ERR_PUSH_NOT_CONVERGED, "push did not converge in %u rounds", b.max_rounds);
   if (*w->h_err & kErrWalkOverflow) return fail(FORA_ERR_WALK_OVERFLOW, "a source needs 2^32 or more walks");
   if (*w->h_err & kErrWalkCap) return fail(FORA_ERR_WALK_CAP, "a walk exceeded %d moves", FORA_MAX_WALK_STEPS);
   if (*w->h_err & kErrIndexRange)
@@ -524,8 +607,8 @@ int fora_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col, uin
   if (cudaGetDevice(&g->device) != cudaSuccess) return bail(fail(FORA_ERR_CUDA, "no CUDA device"));
   if (cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess)
     return bail(fail(FORA_ERR_CUDA, "cannot query the SM count"));
-  cudaError_t e = cudaMalloc(&g->row, ((size_t)n + 1) * sizeof(uint32_t));
-  if (e == cudaSuccess) e = cudaMalloc(&g->col, (size_t)m * sizeof(int32_t));
+  cudaError_t e = dalloc(&g->row, ((size_t)n + 1) * sizeof(uint32_t));
+  if (e == cudaSuccess) e = dalloc(&g->col, (size_t)m * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemcpy(g->row, row.data(), ((size_t)n + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(g->col, col, (size_t)m * sizeof(int32_t), cudaMemcpyHostToDevice);
   // walk copy of col: ceil(log2 n) bits per target when that saves at least a quarter
@@ -542,7 +625,7 @@ int fora_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col, uin
       packed[w] |= (uint32_t)v;
       packed[w + 1] |= (uint32_t)(v >> 32);
     }
-    e = cudaMalloc(&g->colp, words * sizeof(uint32_t));
+    e = dalloc(&g->colp, words * sizeof(uint32_t));
     if (e == cudaSuccess)
       e = cudaMemcpy(g->colp, packed.data(), words * sizeof(uint32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) g->colbits = bits;
@@ -550,11 +633,11 @@ int fora_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col, uin
   if (e == cudaSuccess) {  // reciprocal out-degrees (every d >= 1 here)
     std::vector<double> invd((size_t)n);
     for (int64_t v = 0; v < n; ++v) invd[v] = 1.0 / (double)(row[v + 1] - row[v]);
-    e = cudaMalloc(&g->invd, (size_t)n * sizeof(double));
+    e = dalloc(&g->invd, (size_t)n * sizeof(double));
     if (e == cudaSuccess)
       e = cudaMemcpy(g->invd, invd.data(), (size_t)n * sizeof(double), cudaMemcpyHostToDevice);
   }
-  if (e == cudaSuccess) e = cudaMalloc(&g->indeg, (size_t)n * sizeof(uint32_t));
+  if (e == cudaSuccess) e = dalloc(&g->indeg, (size_t)n * sizeof(uint32_t));
   if (e == cudaSuccess) {
     const GraphDev gd = g->dev();
     e = launch_indegree(gd, g->indeg, g->num_sms, 0);
@@ -641,6 +724,7 @@ int fora_index_build(fora_graph* g, const fora_params* params, void* stream_) {
     std::lock_guard<std::mutex> tlock(g->mu);
     b.spread_width = g->tune.spread_width;
     b.walk_blocks = g->tune.walk_blocks;
+    b.max_rounds = g->tune.max_push_rounds;
   }
   CUDA_TRY(launch_index_residue(gd, w->r, rp.rmax, stream));
   CUDA_TRY(launch_residuals(gd, b, stream));
@@ -655,8 +739,8 @@ int fora_index_build(fora_graph* g, const fora_params* params, void* stream_) {
   dfree(g->idx_off);
   dfree(g->idx_dest);
   g->idx_entries = 0;
-  CUDA_TRY(cudaMalloc(&g->idx_off, ((size_t)g->n + 1) * sizeof(unsigned long long)));
-  CUDA_TRY(cudaMalloc(&g->idx_dest, (size_t)(W ? W : 1) * sizeof(uint32_t)));
+  CUDA_TRY(dalloc(&g->idx_off, ((size_t)g->n + 1) * sizeof(unsigned long long)));
+  CUDA_TRY(dalloc(&g->idx_dest, (size_t)(W ? W : 1) * sizeof(uint32_t)));
   b.walk_dest = g->idx_dest;
   cudaError_t e = launch_walks(gd, b, g->num_sms, stream);
   // the residual offsets of the nodes 0 .. n-1 (every node is an entry), then W
@@ -885,6 +969,12 @@ int fora_graph_tune(fora_graph* g, const char* key, int64_t value) {
   if (strcmp(key, "push_host_loop") == 0) {
     if (value != 0 && value != 1) return fail(FORA_ERR_BAD_ARG, "push_host_loop must be 0 or 1");
     g->tune.push_host_loop = (int)value;
+    return FORA_OK;
+  }
+  if (strcmp(key, "max_push_rounds") == 0) {
+    if (value < 1 || value > (int64_t)kMaxPushRounds)
+      return fail(FORA_ERR_BAD_ARG, "max_push_rounds must be in [1, %u]", kMaxPushRounds);
+    g->tune.max_push_rounds = (uint32_t)value;
     return FORA_OK;
   }
   return fail(FORA_ERR_BAD_ARG, "unknown tuning key '%s'", key);
@@ -1243,7 +1333,27 @@ int fora_graph_tuning(fora_graph* g, const char* key, int64_t* value) {
   if (strcmp(key, "walk_blocks") == 0) { *value = g->tune.walk_blocks; return FORA_OK; }
   if (strcmp(key, "pipeline") == 0) { *value = g->tune.pipeline; return FORA_OK; }
   if (strcmp(key, "push_host_loop") == 0) { *value = g->tune.push_host_loop; return FORA_OK; }
+  if (strcmp(key, "max_push_rounds") == 0) { *value = g->tune.max_push_rounds; return FORA_OK; }
   return fail(FORA_ERR_BAD_ARG, "unknown tuning key '%s'", key);
+}
+
+int fora_workspace_bytes(int64_t n, const int64_t* row_ptr, int32_t nsrc, uint64_t* bytes) {
+  if (n < 1 || n > 0x7FFFFFFF || !row_ptr || nsrc < 1 || nsrc > 65535 || !bytes)
+    return fail(FORA_ERR_BAD_ARG, "bad arguments");
+  uint64_t hub_chunks = 0;
+  for (int64_t v = 0; v < n; ++v) {
+    const int64_t d = row_ptr[v + 1] - row_ptr[v];
+    if (d < 0) return fail(FORA_ERR_BAD_ARG, "row_ptr not monotone at %lld", (long long)v);
+    if ((uint64_t)d > kHubChunk) hub_chunks += ((uint64_t)d + kHubChunk - 1) / kHubChunk;
+  }
+  *bytes = (uint64_t)workspace_sizes(n, hub_chunks, nsrc).total();
+  return FORA_OK;
+}
+
+int fora_debug_fail_alloc(int64_t nth) {
+  if (nth < 0) return fail(FORA_ERR_BAD_ARG, "nth must be >= 0");
+  g_fail_alloc_in.store((long long)nth);
+  return FORA_OK;
 }
 
 const char* fora_last_error(void) { return g_err.c_str(); }

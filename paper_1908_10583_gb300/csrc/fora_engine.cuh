@@ -23,7 +23,7 @@ constexpr uint32_t kErrWalkCap = 1u;
 constexpr uint32_t kErrWalkOverflow = 2u;
 constexpr uint32_t kErrPushNotConverged = 4u;
 constexpr uint32_t kErrIndexRange = 8u;  // a residue needs more walks than the index holds
-constexpr uint32_t kMaxPushRounds = 100000u;
+constexpr uint32_t kMaxPushRounds = 100000u;  // default cap of the push rounds
 
 // Where the push loop stands: the parity of the current frontier queue, the number of
 // rounds done, and the shape of the current frontier.  Kept on the device so the loop
@@ -129,6 +129,7 @@ struct BatchDev {
   int residual_grid;
   int spread_width;  // interleaved segments of the frontier the spread visits at once
   int walk_blocks;   // resident walk blocks per SM (4, 5 or 6)
+  uint32_t max_rounds;  // push rounds allowed before kErrPushNotConverged
 };
 
 // Launch-shape parameters of a graph (set through fora_graph_tune or the autotuner).
@@ -137,10 +138,18 @@ struct Tuning {
   int walk_blocks = 4;
   int push_host_loop = 0;  // 1: rounds launched from a host loop instead of the graph
   int pipeline = 1;        // parts of a batch run on their own streams, pushes staggered
+  uint32_t max_push_rounds = kMaxPushRounds;
 };
 
 // capi.cu: record a failure for fora_last_error() and return `code`.
 int report_error(int code, const char* fmt, ...);
+// capi.cu: resident blocks per SM of `kernel` launched with `threads` threads and no
+// dynamic shared memory on the current device (at least 1; 0 if the query fails).
+// Cached per (device, kernel) under a lock, so concurrent host threads may call it.
+int resident_blocks(const void* kernel, int threads);
+// capi.cu: cudaMalloc through the library's allocation hook (fora_debug_fail_alloc):
+// returns cudaErrorMemoryAllocation without allocating when the hook says so.
+cudaError_t device_alloc(void** p, size_t bytes);
 
 // push.cu: r(s) = 1 and the loop state; then the rounds, each launched by the body of a
 // conditional while-node of a CUDA graph (the body sets the loop condition itself), or,

@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(kTakeThreads, 3) k_push_take(GraphDev g, Batch
 
 // End of a round (one block): the new frontier's per-source group and hub-item prefixes,
 // the list of sources that still push, zeroed counters for the round after, and the
-// loop condition (at most kMaxPushRounds rounds).
+// loop condition (at most b.max_rounds rounds).
 __global__ void __launch_bounds__(1024) k_push_advance(BatchDev b,
                                                        cudaGraphConditionalHandle loop,
                                                        int in_graph) {
@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(1024) k_push_advance(BatchDev b,
     b.work[0] = 0;  // dynamic work counters of the next spread
     b.work[16] = 0;
     const bool more = carry_a > 0;
-    const bool go = more && ps->round < kMaxPushRounds;
+    const bool go = more && ps->round < b.max_rounds;
     if (more && !go) atomicOr(b.err, kErrPushNotConverged);
     ps->go = go ? 1u : 0u;
     if (in_graph) cudaGraphSetConditional(loop, go ? 1u : 0u);
@@ -468,14 +468,6 @@ __global__ void k_threshold_table(const double* r, const double* rm, const uint3
   const float rmf = __double2float_rn(rm[i]);
   const bool fast = rmf >= 0x1p-100f && rmf <= 0x1p60f;
   out[i] = above_threshold(r[i], rm[i], rmf, fast, d[i]) ? 1 : 0;
-}
-
-template <typename K>
-int resident_blocks(K kernel, int threads) {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess)
-    return 0;
-  return per_sm < 1 ? 1 : per_sm;
 }
 
 }  // namespace
@@ -497,9 +489,8 @@ cudaError_t launch_push_body(const GraphDev& g, const BatchDev& b, int num_sms,
                              cudaGraphConditionalHandle loop, bool in_graph, cudaStream_t st) {
   // one wave of resident blocks for the spread (with the dynamic work counter the warps
   // in flight cover one contiguous window of the frontier) and for the take
-  static int spread_per_sm = 0, take_per_sm = 0;
-  if (spread_per_sm == 0) spread_per_sm = resident_blocks(k_push_spread, kSpreadThreads);
-  if (take_per_sm == 0) take_per_sm = resident_blocks(k_push_take, kTakeThreads);
+  const int spread_per_sm = resident_blocks((const void*)k_push_spread, kSpreadThreads);
+  const int take_per_sm = resident_blocks((const void*)k_push_take, kTakeThreads);
   if (spread_per_sm == 0 || take_per_sm == 0) return cudaErrorInvalidConfiguration;
   k_push_spread<<<num_sms * spread_per_sm, kSpreadThreads, 0, st>>>(g, b);
   cudaError_t e = cudaGetLastError();

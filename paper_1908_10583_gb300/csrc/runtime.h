@@ -11,6 +11,22 @@
 
 namespace fora {
 
+// The residual kernels run at most this many blocks (8 per SM on up to 512 SMs), so the
+// per-block scan buffers have a size that does not depend on the device.
+constexpr int kMaxResidualGrid = 4096;
+
+// Device bytes of every buffer of a query workspace for nsrc sources of a graph with n
+// nodes and hub_chunks hub items (workspace_sizes).  The workspace allocates exactly
+// these; the server's admission and fora_workspace_bytes count them.
+struct WorkspaceSizes {
+  size_t N = 0;  // nsrc * n
+  size_t r = 0, res = 0, tally = 0, q = 0, fa = 0, hub = 0, small = 0, work = 0, alist = 0,
+         slot_cnt = 0, pre = 0, ps = 0, err = 0, sources = 0, rmax = 0, stats = 0, blk = 0,
+         topk = 0, feat = 0, pred = 0, rmax_learned = 0, out_ids = 0, out_vals = 0;
+  size_t total() const;  // q and hub count twice (two parities)
+};
+WorkspaceSizes workspace_sizes(int64_t n, uint64_t hub_chunks, int nsrc);
+
 template <typename T>
 void dfree(T*& p) {
   if (p) cudaFree((void*)p);
@@ -23,9 +39,10 @@ struct PushGraphKey {
   int nsrc = 0;
   double alpha = 0.0;
   int spread_width = 0;
+  uint32_t max_rounds = 0;
   bool operator==(const PushGraphKey& o) const {
     return generation == o.generation && nsrc == o.nsrc && alpha == o.alpha &&
-           spread_width == o.spread_width;
+           spread_width == o.spread_width && max_rounds == o.max_rounds;
   }
 };
 

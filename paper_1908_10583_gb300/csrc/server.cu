@@ -10,6 +10,7 @@
 // overlap on the device and slots refill as batches finish.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -49,9 +50,14 @@ bool compatible(const fora_params& a, const fora_params& b) {
          a.rmax == b.rmax && a.seed == b.seed && a.flags == b.flags;
 }
 
-size_t bytes_per_query(const fora_graph* g) {
-  // r, reserve, tally, two frontier queues, increments, hub items, top-k scratch share
-  return (size_t)g->n * 56 + (size_t)g->hub_chunks * 16 + 130 * 1024;
+// The most query slots whose workspace (the same buffer sizes the workspace allocates)
+// fits `share` bytes, at most `cap`; 0 if not even one fits.
+int slots_within(const fora_graph* g, size_t share, int cap) {
+  const size_t one = workspace_sizes(g->n, g->hub_chunks, 1).total();
+  if (one > share) return 0;
+  const size_t per = workspace_sizes(g->n, g->hub_chunks, 2).total() - one;  // linear in slots
+  const size_t more = per ? (share - one) / per : (size_t)cap;
+  return (int)std::min<size_t>((size_t)cap, 1 + more);
 }
 
 }  // namespace
@@ -187,15 +193,14 @@ int fora_server_create(fora_graph* const* graphs, int32_t ngraphs, const fora_se
   // query slots as that share holds
   const size_t share = budget / ((size_t)ngraphs * cfg->lanes_per_graph);
   for (int gi = 0; gi < ngraphs; ++gi) {
-    const size_t per = bytes_per_query(graphs[gi]);
-    const size_t slots = share / per;
+    const int slots = slots_within(graphs[gi], share, cfg->max_batch);
     if (slots < 1)
       return report_error(FORA_ERR_OOM, "memory budget too small for one query of graph %d", gi);
     for (int l = 0; l < cfg->lanes_per_graph; ++l) {
       auto L = std::make_unique<Lane>();
       L->graph = gi;
       L->index = (int)s->lanes.size();
-      L->cap = (int)(slots < (size_t)cfg->max_batch ? slots : (size_t)cfg->max_batch);
+      L->cap = slots;
       if (cudaSetDevice(graphs[gi]->device) != cudaSuccess ||
           cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking) != cudaSuccess)
         return report_error(FORA_ERR_CUDA, "cannot create a lane stream");

@@ -525,13 +525,8 @@ cudaError_t launch_residuals(const GraphDev& g, const BatchDev& b, cudaStream_t 
 // register budget the compiler gets); b.walk_blocks picks one (launch shape only).
 template <int kMinBlocks>
 cudaError_t launch_walks_t(const GraphDev& g, const BatchDev& b, int num_sms, cudaStream_t st) {
-  static int per_sm = 0;
-  if (per_sm == 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walks<kMinBlocks>,
-                                                                  kWalkThreads, 0);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-  }
+  const int per_sm = resident_blocks((const void*)k_walks<kMinBlocks>, kWalkThreads);
+  if (per_sm == 0) return cudaErrorInvalidConfiguration;
   k_walks<kMinBlocks><<<num_sms * per_sm, kWalkThreads, 0, st>>>(g, b);
   return cudaGetLastError();
 }
@@ -552,11 +547,8 @@ cudaError_t launch_index_residue(const GraphDev& g, double* r, double rmax, cuda
 cudaError_t launch_walks_indexed(const GraphDev& g, const BatchDev& b, int num_sms,
                                  const unsigned long long* idx_off, const uint32_t* idx_dest,
                                  cudaStream_t st) {
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walks_indexed,
-                                                                kWalkThreads, 0);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
+  const int per_sm = resident_blocks((const void*)k_walks_indexed, kWalkThreads);
+  if (per_sm == 0) return cudaErrorInvalidConfiguration;
   k_walks_indexed<<<num_sms * per_sm, kWalkThreads, 0, st>>>(g, b, idx_off, idx_dest);
   return cudaGetLastError();
 }

@@ -397,8 +397,11 @@ def test_pipelined_batch_equals_one_part(rmat14):
             ids2, vals2, st2 = g.ssppr_batch(sources, p)
             assert [s.walks for s in st2] == [s.walks for s in st1]
             assert [s.pushes for s in st2] == [s.pushes for s in st1]
-            np.testing.assert_allclose(vals2, vals1, rtol=0, atol=2e-12)
-            assert (ids2 == ids1).mean() > 0.99  # ids may swap only between near-equal values
+            np.testing.assert_allclose(vals2, vals1, rtol=0, atol=ATOL_PUSH)
+            # ids may differ only where the two estimates at that rank are equal within the
+            # push tolerance (two near-equal nodes swapping places)
+            differ = ids2 != ids1
+            assert np.all(np.abs(vals2[differ] - vals1[differ]) <= 2 * ATOL_PUSH)
     finally:
         g.tune("pipeline", 1)
     with pytest.raises(fora.FORAError):

@@ -62,3 +62,44 @@ def test_features_by_hand():
     want = [math.log1p(3), math.log1p(3), math.log1p(4), math.log1p(4), math.log1p(2),
             math.log1p(2), math.log(0.15 * 7), math.log(7 / 4)] + [0.0] * 8
     np.testing.assert_allclose(f, np.array(want, dtype=np.float32), rtol=1e-7)
+
+
+def hand_network():
+    """Parameters and one input of a 16-64-64-1 network worked by hand, where every BF16
+    rounding point of the forward pass changes the output if it is dropped or moved.
+    Only unit 0 of each layer is used (every other weight and bias is 0), mu = 0,
+    sigma = 1, and the input is f0 = 1 + 2^-8 (other features 0).  BF16 keeps 8
+    significant bits, so near 1 its values are 1, 1 + 2^-7, ... and 1 + 2^-8 is a tie
+    that rounds to even (1.0).  Masters: W1[0][0] = W2[0][0] = W3[0] = 1 + 2^-8 (BF16:
+    1.0), b1[0] = b2[0] = 2^-8 + 2^-17 (BF16: 2^-8), b3 = 2^-12 + 2^-25 (BF16: 2^-12).
+    With every rounding in place: x0 = 1, z1 = 1 + 2^-8 -> h1 = 1 (tie), z2 = 1 + 2^-8
+    -> h2 = 1 (tie), y = 1 + 2^-12 (the output is not rounded)."""
+    p = np.zeros(learn.N_PARAMS, dtype=np.float32)
+    p[learn.OFF_W1 + 0] = 1 + 2.0 ** -8
+    p[learn.OFF_B1 + 0] = 2.0 ** -8 + 2.0 ** -17
+    p[learn.OFF_W2 + 0] = 1 + 2.0 ** -8
+    p[learn.OFF_B2 + 0] = 2.0 ** -8 + 2.0 ** -17
+    p[learn.OFF_W3 + 0] = 1 + 2.0 ** -8
+    p[learn.OFF_B3] = 2.0 ** -12 + 2.0 ** -25
+    norm = np.concatenate([np.zeros(16), np.ones(16)]).astype(np.float32)
+    x = np.zeros((1, 16), dtype=np.float32)
+    x[0, 0] = 1 + 2.0 ** -8
+    return p, norm, x
+
+
+def test_forward_rounding_points_by_hand():
+    """Each misplaced rounding gives another output: dropping the input rounding makes
+    z1 = 1 + 2^-7 (h1 = 1 + 2^-7, y about 1.0078); unrounded W1 or b1 push z1 above the
+    tie (h1 = 1 + 2^-7); an unrounded h1 makes z2 = 1 + 2^-7; an unrounded W2 or b2 push
+    z2 above its tie; an unrounded h2 gives y = 1 + 2^-8 + 2^-12; unrounded W3 or b3 add
+    2^-8 or 2^-25; rounding y itself would give 1.0."""
+    p, norm, x = hand_network()
+    y, _ = learn.forward(p, norm, x, rounding=True)
+    assert y[0] == 1 + 2.0 ** -12
+    # without any rounding: the exact FP64 value of the same arithmetic
+    e = 1 + 2.0 ** -8
+    z1 = e * e + 2.0 ** -8 + 2.0 ** -17
+    z2 = e * z1 + 2.0 ** -8 + 2.0 ** -17
+    want = e * z2 + 2.0 ** -12 + 2.0 ** -25
+    y_u, _ = learn.forward(p.astype(np.float64), norm, x, rounding=False)
+    assert y_u[0] == want

@@ -368,6 +368,7 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
     b.spread_width = g->tune.spread_width;
     b.walk_blocks = g->tune.walk_blocks;
     b.max_rounds = g->tune.max_push_rounds;
+    b.walk_variant = g->tune.walk_variant;
     host_loop = g->tune.push_host_loop != 0;
   }
 
@@ -637,6 +638,13 @@ int fora_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col, uin
     if (e == cudaSuccess)
       e = cudaMemcpy(g->invd, invd.data(), (size_t)n * sizeof(double), cudaMemcpyHostToDevice);
   }
+  if (e == cudaSuccess) {  // the walks' node records {first edge, out-degree}
+    std::vector<uint2> rd((size_t)n);
+    for (int64_t v = 0; v < n; ++v) rd[v] = make_uint2(row[v], row[v + 1] - row[v]);
+    e = dalloc(&g->rd, (size_t)n * sizeof(uint2));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(g->rd, rd.data(), (size_t)n * sizeof(uint2), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = dalloc(&g->indeg, (size_t)n * sizeof(uint32_t));
   if (e == cudaSuccess) {
     const GraphDev gd = g->dev();
@@ -666,6 +674,7 @@ void fora_graph_destroy(fora_graph* g) {
     dfree(g->colp);
     dfree(g->indeg);
     dfree(g->invd);
+    dfree(g->rd);
     dfree(g->idx_off);
     dfree(g->idx_dest);
   }
@@ -725,6 +734,7 @@ int fora_index_build(fora_graph* g, const fora_params* params, void* stream_) {
     b.spread_width = g->tune.spread_width;
     b.walk_blocks = g->tune.walk_blocks;
     b.max_rounds = g->tune.max_push_rounds;
+    b.walk_variant = g->tune.walk_variant;
   }
   CUDA_TRY(launch_index_residue(gd, w->r, rp.rmax, stream));
   CUDA_TRY(launch_residuals(gd, b, stream));
@@ -969,6 +979,11 @@ int fora_graph_tune(fora_graph* g, const char* key, int64_t value) {
   if (strcmp(key, "push_host_loop") == 0) {
     if (value != 0 && value != 1) return fail(FORA_ERR_BAD_ARG, "push_host_loop must be 0 or 1");
     g->tune.push_host_loop = (int)value;
+    return FORA_OK;
+  }
+  if (strcmp(key, "walk_variant") == 0) {
+    if (value < 0 || value > 2) return fail(FORA_ERR_BAD_ARG, "walk_variant must be 0, 1 or 2");
+    g->tune.walk_variant = (int)value;
     return FORA_OK;
   }
   if (strcmp(key, "max_push_rounds") == 0) {
@@ -1334,6 +1349,7 @@ int fora_graph_tuning(fora_graph* g, const char* key, int64_t* value) {
   if (strcmp(key, "pipeline") == 0) { *value = g->tune.pipeline; return FORA_OK; }
   if (strcmp(key, "push_host_loop") == 0) { *value = g->tune.push_host_loop; return FORA_OK; }
   if (strcmp(key, "max_push_rounds") == 0) { *value = g->tune.max_push_rounds; return FORA_OK; }
+  if (strcmp(key, "walk_variant") == 0) { *value = g->tune.walk_variant; return FORA_OK; }
   return fail(FORA_ERR_BAD_ARG, "unknown tuning key '%s'", key);
 }
 

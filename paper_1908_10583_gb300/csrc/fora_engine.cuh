@@ -47,6 +47,7 @@ struct GraphDev {
   const uint32_t* colp;
   int colbits;
   const double* invd;   // [n] RN(1 / d(v)): the push increment is a product, not a quotient
+  const uint2* rd;      // [n] {row[v], d(v)}: a walk's move reads one aligned 8-byte record
 };
 
 // Target e of a bit-packed column array (two 32-bit words always readable).
@@ -130,6 +131,8 @@ struct BatchDev {
   int spread_width;  // interleaved segments of the frontier the spread visits at once
   int walk_blocks;   // resident walk blocks per SM (4, 5 or 6)
   uint32_t max_rounds;  // push rounds allowed before kErrPushNotConverged
+  int walk_variant;     // walk kernel: 0 one word per step, 1 one Philox block per step,
+                        // 2 the same with warp-aggregated tally atomics
 };
 
 // Launch-shape parameters of a graph (set through fora_graph_tune or the autotuner).
@@ -139,6 +142,7 @@ struct Tuning {
   int push_host_loop = 0;  // 1: rounds launched from a host loop instead of the graph
   int pipeline = 1;        // parts of a batch run on their own streams, pushes staggered
   uint32_t max_push_rounds = kMaxPushRounds;
+  int walk_variant = 0;
 };
 
 // capi.cu: record a failure for fora_last_error() and return `code`.

@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(kTakeThreads, 3) k_push_take(GraphDev g, Batch
 
 // End of a round (one block): the new frontier's per-source group and hub-item prefixes,
 // the list of sources that still push, zeroed counters for the round after, and the
-// loop condition (at most b.max_rounds rounds).
+// loop condition (at most b.max_rounds push rounds).
 __global__ void __launch_bounds__(1024) k_push_advance(BatchDev b,
                                                        cudaGraphConditionalHandle loop,
                                                        int in_graph) {
@@ -452,8 +452,10 @@ __global__ void __launch_bounds__(1024) k_push_advance(BatchDev b,
     ps->round += 1;
     b.work[0] = 0;  // dynamic work counters of the next spread
     b.work[16] = 0;
+    // ps->round passes have run; the last one took the frontier of push round ps->round
+    // (the first pass only finds F_0), so going on is allowed while that is <= the cap
     const bool more = carry_a > 0;
-    const bool go = more && ps->round < b.max_rounds;
+    const bool go = more && ps->round <= b.max_rounds;
     if (more && !go) atomicOr(b.err, kErrPushNotConverged);
     ps->go = go ? 1u : 0u;
     if (in_graph) cudaGraphSetConditional(loop, go ? 1u : 0u);

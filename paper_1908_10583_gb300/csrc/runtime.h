@@ -165,6 +165,7 @@ struct fora_graph {
   int colbits = 0;
   uint32_t* indeg = nullptr;  // in-degrees (features of the learned r_max)
   double* invd = nullptr;     // RN(1 / d(v)) per node
+  uint2* rd = nullptr;        // {row[v], d(v)} per node (the walks' node record)
   // FORA+ walk index (Section 3.3): ends of omega_max(v) walks from every v
   unsigned long long* idx_off = nullptr;  // [n + 1] exclusive prefix of omega_max
   uint32_t* idx_dest = nullptr;           // [idx_entries] walk ends
@@ -180,7 +181,7 @@ struct fora_graph {
   // parts of a pipelined batch: a workspace and a stream each
   fora::Workspace pipe_ws[fora::kMaxPipeline];
   cudaStream_t pipe_stream[fora::kMaxPipeline] = {};
-  fora::GraphDev dev() const { return fora::GraphDev{n, m, row, col, colp, colbits, invd}; }
+  fora::GraphDev dev() const { return fora::GraphDev{n, m, row, col, colp, colbits, invd, rd}; }
 };
 
 namespace fora {

@@ -422,6 +422,226 @@ __global__ void __launch_bounds__(kWalkThreads, kMinBlocks) k_walks(GraphDev g, 
   if (steps_here) atomicAdd(&b.stats[cur_slot].walk_steps, steps_here);
 }
 
+// Map walk cbeg + i (i < cnt) to its residual entry idx0 + smap[i], 32 walks at a time
+// (the entries' walk offsets are read coalesced, a 5-step search per walk in registers).
+__device__ __forceinline__ void map_chunk(const unsigned long long* off, unsigned long long nR,
+                                          unsigned long long cbeg, uint32_t cnt,
+                                          unsigned long long idx0, uint16_t* smap) {
+  const uint32_t lane = threadIdx.x & 31;
+  unsigned long long idxw = idx0;
+  for (uint32_t rb = 0; rb < cnt; rb += 32) {
+    const unsigned long long gw = cbeg + rb + lane;
+    const unsigned long long o = idxw + lane < nR ? off[idxw + lane] : ~0ull;
+    int lo = 0, hi = 31;  // largest j with off[idxw + j] <= gw
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__shfl_sync(kFull, o, mid) <= gw) lo = mid; else hi = mid - 1;
+    }
+    const unsigned long long mine = idxw + (unsigned long long)lo;
+    smap[rb + lane] = (uint16_t)(mine - idx0);
+    idxw = __shfl_sync(kFull, mine, 31);
+  }
+  __syncwarp();
+}
+
+// Target e of the walk copy of the adjacency (bit-packed when colbits > 0).
+__device__ __forceinline__ uint32_t walk_target(const GraphDev& g, uint32_t e) {
+  return g.colbits ? packed_target(g.colp, g.colbits, e) : (uint32_t)g.col[e];
+}
+
+constexpr uint32_t kCapped = 0xFFFFFFFFu;
+
+// The rest of a walk after the first try of a neighbour draw was rejected (Lemire's
+// method rejects a try with probability below d / 2^32): the walk's words are taken one
+// at a time from word `pos` of the block `blk` (the next block to generate is `cb`), first
+// for the retries of the move at x (row offset rb, degree d), then for the stop tests and
+// moves that follow, exactly in stream order.  Returns the end node, or kCapped when the
+// walk reaches the step cap (or, never in practice, 64 rejected tries in a row).
+__device__ __forceinline__ uint32_t walk_rest(const GraphDev& g, uint4 blk, int pos, uint32_t cb,
+                                           uint32_t j, uint32_t v, uint32_t s, uint2 key,
+                                           uint32_t t_alpha, uint32_t x, uint32_t rb, uint32_t d,
+                                           uint32_t* steps) {
+  auto next = [&]() -> uint32_t {
+    if (pos == 4) {
+      blk = philox4x32_10(make_uint4(cb, j, v, s), key);
+      ++cb;
+      pos = 0;
+    }
+    const uint32_t w = pos == 0 ? blk.x : pos == 1 ? blk.y : pos == 2 ? blk.z : blk.w;
+    ++pos;
+    return w;
+  };
+  bool retry = true;  // the move at x still needs an accepted try
+  for (;;) {
+    if (!retry) {
+      if (next() < t_alpha) return x;
+      if (*steps >= kMaxSteps) return kCapped;
+      const uint2 r = g.rd[x];
+      rb = r.x;
+      d = r.y;
+    }
+    unsigned long long m = (unsigned long long)next() * d;
+    uint32_t low = (uint32_t)m;
+    const uint32_t reject_below = (0u - d) % d;
+    int tries = 0;
+    while (low < reject_below) {
+      if (++tries > 64) return kCapped;
+      m = (unsigned long long)next() * d;
+      low = (uint32_t)m;
+    }
+    retry = false;
+    x = walk_target(g, rb + (uint32_t)(m >> 32));
+    ++*steps;
+  }
+}
+
+// One move of a walk at x with the word u, on the fast path: returns false when the try
+// is rejected (the walk then finishes in walk_rest) and leaves rb, d for it.
+__device__ __forceinline__ bool fast_move(const GraphDev& g, uint32_t u, uint32_t& x,
+                                          uint32_t& rb, uint32_t& d) {
+  const uint2 r = g.rd[x];
+  rb = r.x;
+  d = r.y;
+  const unsigned long long m = (unsigned long long)u * d;
+  const uint32_t low = (uint32_t)m;
+  if (low < d && low < (0u - d) % d) return false;
+  x = walk_target(g, rb + (uint32_t)(m >> 32));
+  return true;
+}
+
+// The walk kernel.  Walks are scheduled as in k_walks (chunks of kChunk walks round-robin
+// over the warps, a shared-memory map from walk to residual entry, a lane taking the
+// chunk's next unstarted walk when its walk ends), but one loop iteration consumes exactly
+// one Philox block of a lane's walk: the words of block c are, in stream order, a stop
+// test and a move, then another stop test and move (plain walks: T M T M), or a move and a
+// stop test twice (zero-hop walks, whose first move has no stop test: M T M T).  So every
+// lane with a walk evaluates its Philox block in the same iteration, and the 10-round
+// block, most of a walk's arithmetic, runs on full warps.  A walk that stops inside a
+// block leaves the block's remaining words unused, as its stream definition does.  A
+// rejected neighbour try (probability below d / 2^32) moves the walk off this block
+// alignment: walk_rest then finishes it word by word.  Walk ends of a warp that fall on the
+// same tally with the same weight are summed before one atomic (kAggregate).
+template <int kMinBlocks, bool kZeroHop, bool kAggregate>
+__global__ void __launch_bounds__(kWalkThreads, kMinBlocks) k_walks_blk(GraphDev g, BatchDev b) {
+  __shared__ uint16_t smap[kWalkWarps][kChunk];
+  if (*b.err) return;
+  const unsigned long long W = b.totals[1];
+  const unsigned long long nR = b.totals[0];
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  const unsigned long long nchunks = (W + kChunk - 1) / kChunk;
+  const unsigned long long* off = b.wr_offset;
+  const unsigned long long n = (unsigned long long)g.n;
+  const uint2 key = make_uint2((uint32_t)b.seed, (uint32_t)(b.seed >> 32));
+  const uint32_t t_alpha = b.alpha_threshold;
+  unsigned long long steps_here = 0;  // moves of this lane's walks of source `cur_slot`
+  uint32_t cur_slot = 0xFFFFFFFFu;
+  bool capped = false;
+
+  for (unsigned long long c = warp; c < nchunks; c += nwarps) {
+    const unsigned long long cbeg = c * kChunk;
+    const uint32_t cnt = (uint32_t)min((unsigned long long)kChunk, W - cbeg);
+    const unsigned long long idx0 = warp_find_entry(off, nR, cbeg);
+    map_chunk(off, nR, cbeg, cnt, idx0, smap[wid]);
+
+    uint32_t next_walk = 32;  // warp-uniform: the chunk's next unstarted walk
+    uint32_t i = lane;
+    bool have = i < cnt;
+    uint32_t x = 0, v = 0, j = 0, s = 0, slot = 0, steps = 0, cb = 0;
+    unsigned long long wgt = 0;
+    auto start = [&]() {
+      const unsigned long long idx = idx0 + smap[wid][i];
+      const unsigned long long entry = b.wr_entry[idx];
+      slot = (uint32_t)(entry >> 32);
+      v = (uint32_t)entry;
+      x = v;
+      j = (uint32_t)(cbeg + i - off[idx]);
+      s = (uint32_t)b.sources[slot];
+      wgt = b.wr_weight[idx];
+      steps = 0;
+      cb = 0;
+    };
+    if (have) start();
+    for (;;) {
+      bool stop = false;
+      if (have) {
+        const uint4 o = philox4x32_10(make_uint4(cb, j, v, s), key);
+        ++cb;
+        uint32_t rb = 0, d = 0;
+        int rejected = -1;  // word index of a rejected try
+        if (!kZeroHop) {
+          stop = o.x < t_alpha;
+          if (!stop) {
+            if (steps >= kMaxSteps) { capped = true; have = false; }
+            else if (fast_move(g, o.y, x, rb, d)) { ++steps; stop = o.z < t_alpha; }
+            else rejected = 1;
+          }
+          if (have && !stop && rejected < 0) {
+            if (steps >= kMaxSteps) { capped = true; have = false; }
+            else if (fast_move(g, o.w, x, rb, d)) ++steps;
+            else rejected = 3;
+          }
+        } else {
+          if (steps >= kMaxSteps) { capped = true; have = false; }
+          else if (fast_move(g, o.x, x, rb, d)) { ++steps; stop = o.y < t_alpha; }
+          else rejected = 0;
+          if (have && !stop && rejected < 0) {
+            if (steps >= kMaxSteps) { capped = true; have = false; }
+            else if (fast_move(g, o.z, x, rb, d)) { ++steps; stop = o.w < t_alpha; }
+            else rejected = 2;
+          }
+        }
+        if (rejected >= 0) {  // rare: finish the walk word by word
+          const uint32_t end = walk_rest(g, o, rejected + 1, cb, j, v, s, key, t_alpha, x, rb, d,
+                                         &steps);
+          if (end == kCapped) { capped = true; have = false; }
+          else { x = end; stop = true; }
+        }
+      }
+      const bool ended = have && stop;
+      const uint32_t ends = __ballot_sync(kFull, ended);
+      if (ended) {
+        // the walk stops at x (Section 2.1): count it and add its weight (Alg. 2), or
+        // record its end in a walk index (Section 3.3)
+        if (b.walk_dest) {
+          b.walk_dest[cbeg + i] = x;
+        } else {
+          Tally* t = b.tally + (unsigned long long)slot * n + x;
+          if (kAggregate) {
+            const unsigned grp = __match_any_sync(ends, (unsigned long long)t) &
+                                 __match_any_sync(ends, wgt);
+            if ((grp & lt_mask) == 0) {  // the group's lowest lane adds for all of it
+              const uint32_t k = (uint32_t)__popc(grp);
+              if (b.want_count) atomicAdd(&t->cnt, k);
+              atomicAdd(&t->acc, wgt * (unsigned long long)k);
+            }
+          } else {
+            if (b.want_count) atomicAdd(&t->cnt, 1u);
+            atomicAdd(&t->acc, wgt);
+          }
+        }
+        if (slot != cur_slot) {
+          if (steps_here) atomicAdd(&b.stats[cur_slot].walk_steps, steps_here);
+          steps_here = 0;
+          cur_slot = slot;
+        }
+        steps_here += steps;
+        i = next_walk + (uint32_t)__popc(ends & lt_mask);
+        have = i < cnt;
+        if (have) start();
+      }
+      next_walk += (uint32_t)__popc(ends);
+      if (!__any_sync(kFull, have)) break;
+    }
+    __syncwarp();
+  }
+  if (capped) atomicOr(b.err, kErrWalkCap);
+  if (steps_here) atomicAdd(&b.stats[cur_slot].walk_steps, steps_here);
+}
+
 // FORA+ (Section 3.3): the residue whose walk count is the index's omega_max(v).
 __global__ void k_index_residue(GraphDev g, double* r, double rmax) {
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
@@ -531,7 +751,32 @@ cudaError_t launch_walks_t(const GraphDev& g, const BatchDev& b, int num_sms, cu
   return cudaGetLastError();
 }
 
+template <int kMinBlocks, bool kZeroHop, bool kAggregate>
+cudaError_t launch_walks_blk_t(const GraphDev& g, const BatchDev& b, int num_sms,
+                               cudaStream_t st) {
+  const void* k = (const void*)k_walks_blk<kMinBlocks, kZeroHop, kAggregate>;
+  const int per_sm = resident_blocks(k, kWalkThreads);
+  if (per_sm == 0) return cudaErrorInvalidConfiguration;
+  k_walks_blk<kMinBlocks, kZeroHop, kAggregate><<<num_sms * per_sm, kWalkThreads, 0, st>>>(g, b);
+  return cudaGetLastError();
+}
+
+template <bool kZeroHop, bool kAggregate>
+cudaError_t launch_walks_blk(const GraphDev& g, const BatchDev& b, int num_sms, cudaStream_t st) {
+  switch (b.walk_blocks) {
+    case 6: return launch_walks_blk_t<6, kZeroHop, kAggregate>(g, b, num_sms, st);
+    case 5: return launch_walks_blk_t<5, kZeroHop, kAggregate>(g, b, num_sms, st);
+    default: return launch_walks_blk_t<4, kZeroHop, kAggregate>(g, b, num_sms, st);
+  }
+}
+
 cudaError_t launch_walks(const GraphDev& g, const BatchDev& b, int num_sms, cudaStream_t st) {
+  if (b.walk_variant == 1)
+    return b.zero_hop ? launch_walks_blk<true, false>(g, b, num_sms, st)
+                      : launch_walks_blk<false, false>(g, b, num_sms, st);
+  if (b.walk_variant == 2)
+    return b.zero_hop ? launch_walks_blk<true, true>(g, b, num_sms, st)
+                      : launch_walks_blk<false, true>(g, b, num_sms, st);
   switch (b.walk_blocks) {
     case 6: return launch_walks_t<6>(g, b, num_sms, st);
     case 5: return launch_walks_t<5>(g, b, num_sms, st);

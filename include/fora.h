@@ -373,8 +373,8 @@ int fora_threshold_debug(const double *r, const double *rmax, const uint32_t *d,
  * speed):  "spread_width" (1..4096, default 1): the push visits the frontier of a round
  * (grouped by source) through this many interleaved segments, so the warps in flight cover about that
  * many sources at once (wider spreads reductions on shared hub targets over more
- * addresses; narrower keeps the residue arrays in flight smaller).  "walk_blocks" (4, 5
- * or 6, default 4): resident walk blocks per SM, traded against registers per thread.
+ * addresses; narrower keeps the residue arrays in flight smaller).  "walk_blocks" (3, 4
+ * or 5, default 3): resident walk blocks per SM, traded against registers per thread.
  * "push_host_loop" (0 or 1, default 0): 1 launches the push rounds from a host loop with
  * one device-to-host read per round, instead of the CUDA graph whose conditional while-node
  * runs them on the device; the kernels are the same (a profiler that cannot look inside
@@ -398,7 +398,7 @@ int fora_graph_tuning(fora_graph *g, const char *key, int64_t *value);
  * Autotuner over the launch shapes of fora_graph_tune: runs the batched query on the
  * given sources (HOST array, a representative batch) once to warm up, then with
  * spread_width 1, 2, 4, 8, 16 keeping the fastest push phase, then with walk_blocks
- * 4, 5, 6 ("walk_blocks": resident 256-thread walk blocks per SM, i.e. the register
+ * 3, 4, 5 ("walk_blocks": resident 256-thread walk blocks per SM, i.e. the register
  * budget of the walk kernel) keeping the fastest walk phase (both with "pipeline" 1),
  * then, for nsrc >= 64, "pipeline" 1 or 2 by the whole batch's time (the faster of two
  * runs each).  The choices stay set on the graph; spread_width and walk_blocks are

@@ -186,6 +186,18 @@ int ensure_workspace(fora_graph* g, Workspace* w, int nsrc) {
   return FORA_OK;
 }
 
+// The ten Philox4x32-10 round keys of a 64-bit seed (Salmon et al.: the key (lo, hi) is
+// bumped by (0x9E3779B9, 0xBB67AE85) after every round), kept in the kernel parameters so
+// that the walk kernels read them as constants.
+void set_round_keys(BatchDev* b, uint64_t seed) {
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int i = 0; i < 10; ++i) {
+    b->round_key[i] = make_uint2(k0, k1);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
 // Parameters as a query resolves them (Alg. 2; Eq. rmax and Case 2, Section 3.2).
 struct Resolved {
   double alpha, eps, delta, pf, rmax, walk_scale;
@@ -342,6 +354,7 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
   b.walk_scale = rp.walk_scale;
   b.alpha_threshold = rp.alpha_threshold;
   b.seed = p->seed;
+  set_round_keys(&b, p->seed);
   b.zero_hop = (p->flags & FORA_ZERO_HOP) != 0;
   b.want_count = dbg && dbg->count;
   b.r = w->r; b.res = w->res; b.tally = w->tally;
@@ -368,7 +381,6 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
     b.spread_width = g->tune.spread_width;
     b.walk_blocks = g->tune.walk_blocks;
     b.max_rounds = g->tune.max_push_rounds;
-    b.walk_variant = g->tune.walk_variant;
     host_loop = g->tune.push_host_loop != 0;
   }
 
@@ -709,6 +721,7 @@ int fora_index_build(fora_graph* g, const fora_params* params, void* stream_) {
   b.walk_scale = rp.walk_scale;
   b.alpha_threshold = rp.alpha_threshold;
   b.seed = params->seed;
+  set_round_keys(&b, params->seed);
   // zero-hop: omega_max from (1 - alpha) RN(r_max d(v)) and walks with a forced first move
   b.zero_hop = zero_hop ? 1 : 0;
   b.r = w->r; b.res = w->res; b.tally = w->tally;
@@ -734,7 +747,6 @@ int fora_index_build(fora_graph* g, const fora_params* params, void* stream_) {
     b.spread_width = g->tune.spread_width;
     b.walk_blocks = g->tune.walk_blocks;
     b.max_rounds = g->tune.max_push_rounds;
-    b.walk_variant = g->tune.walk_variant;
   }
   CUDA_TRY(launch_index_residue(gd, w->r, rp.rmax, stream));
   CUDA_TRY(launch_residuals(gd, b, stream));
@@ -967,7 +979,7 @@ int fora_graph_tune(fora_graph* g, const char* key, int64_t value) {
     return FORA_OK;
   }
   if (strcmp(key, "walk_blocks") == 0) {
-    if (value < 4 || value > 6) return fail(FORA_ERR_BAD_ARG, "walk_blocks must be 4, 5 or 6");
+    if (value < 3 || value > 5) return fail(FORA_ERR_BAD_ARG, "walk_blocks must be 3, 4 or 5");
     g->tune.walk_blocks = (int)value;
     return FORA_OK;
   }
@@ -979,11 +991,6 @@ int fora_graph_tune(fora_graph* g, const char* key, int64_t value) {
   if (strcmp(key, "push_host_loop") == 0) {
     if (value != 0 && value != 1) return fail(FORA_ERR_BAD_ARG, "push_host_loop must be 0 or 1");
     g->tune.push_host_loop = (int)value;
-    return FORA_OK;
-  }
-  if (strcmp(key, "walk_variant") == 0) {
-    if (value < 0 || value > 2) return fail(FORA_ERR_BAD_ARG, "walk_variant must be 0, 1 or 2");
-    g->tune.walk_variant = (int)value;
     return FORA_OK;
   }
   if (strcmp(key, "max_push_rounds") == 0) {
@@ -1275,7 +1282,7 @@ int fora_graph_autotune(fora_graph* g, const fora_params* params, const int32_t*
   int rc = run(&pm, &wm);  // warm-up: workspace and push-loop graph
   if (rc) return rc;
   // the push depends on spread_width only, the walk kernel on walk_blocks only
-  int best_sw = 1, best_wb = 4;
+  int best_sw = 1, best_wb = 3;
   float best = 0;
   const int widths[] = {1, 2, 4, 8, 16};
   for (int i = 0; i < 5; ++i) {
@@ -1291,14 +1298,14 @@ int fora_graph_autotune(fora_graph* g, const fora_params* params, const int32_t*
     std::lock_guard<std::mutex> lock(g->mu);
     g->tune.spread_width = best_sw;
   }
-  for (int wb = 4; wb <= 6; ++wb) {
+  for (int wb = 3; wb <= 5; ++wb) {
     {
       std::lock_guard<std::mutex> lock(g->mu);
       g->tune.walk_blocks = wb;
     }
     rc = run(&pm, &wm);
     if (rc) return rc;
-    if (wb == 4 || wm < best) { best = wm; best_wb = wb; }
+    if (wb == 3 || wm < best) { best = wm; best_wb = wb; }
   }
   {
     std::lock_guard<std::mutex> lock(g->mu);
@@ -1349,7 +1356,6 @@ int fora_graph_tuning(fora_graph* g, const char* key, int64_t* value) {
   if (strcmp(key, "pipeline") == 0) { *value = g->tune.pipeline; return FORA_OK; }
   if (strcmp(key, "push_host_loop") == 0) { *value = g->tune.push_host_loop; return FORA_OK; }
   if (strcmp(key, "max_push_rounds") == 0) { *value = g->tune.max_push_rounds; return FORA_OK; }
-  if (strcmp(key, "walk_variant") == 0) { *value = g->tune.walk_variant; return FORA_OK; }
   return fail(FORA_ERR_BAD_ARG, "unknown tuning key '%s'", key);
 }
 

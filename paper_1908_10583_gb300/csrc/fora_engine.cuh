@@ -96,6 +96,7 @@ struct BatchDev {
   double walk_scale;         // C = omega / r_sum
   uint32_t alpha_threshold;  // floor(alpha * 2^32)
   uint64_t seed;
+  uint2 round_key[10];       // Philox round keys of `seed` (key + i * (0x9E3779B9, 0xBB67AE85))
   int zero_hop;              // walk phase with zero-hop pruning (Section 4.1)
   int want_count;            // tally walk counts too (only a debug output reads them)
   uint32_t* walk_dest;       // non-null: k_walks stores walk g's end in walk_dest[g]
@@ -129,20 +130,17 @@ struct BatchDev {
   unsigned long long* totals;     // [2]: |R|, W
   int residual_grid;
   int spread_width;  // interleaved segments of the frontier the spread visits at once
-  int walk_blocks;   // resident walk blocks per SM (4, 5 or 6)
+  int walk_blocks;   // resident walk blocks per SM (3, 4 or 5)
   uint32_t max_rounds;  // push rounds allowed before kErrPushNotConverged
-  int walk_variant;     // walk kernel: 0 one word per step, 1 one Philox block per step,
-                        // 2 the same with warp-aggregated tally atomics
 };
 
 // Launch-shape parameters of a graph (set through fora_graph_tune or the autotuner).
 struct Tuning {
   int spread_width = 1;
-  int walk_blocks = 4;
+  int walk_blocks = 3;
   int push_host_loop = 0;  // 1: rounds launched from a host loop instead of the graph
   int pipeline = 1;        // parts of a batch run on their own streams, pushes staggered
   uint32_t max_push_rounds = kMaxPushRounds;
-  int walk_variant = 0;
 };
 
 // capi.cu: record a failure for fora_last_error() and return `code`.

@@ -31,29 +31,17 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
   return c;
 }
 
-// The word stream of one walk: blocks c = 0, 1, ... of Philox with counter (c, j, v, s).
-struct WalkStream {
-  uint32_t c, j, v, s;
-  uint2 key;
-  uint32_t w0, w1, w2, w3;
-  int avail;
-  __device__ __forceinline__ void reset(uint32_t jj, uint32_t vv, uint32_t ss) {
-    c = 0; j = jj; v = vv; s = ss;
-    avail = 0;
+// Philox4x32-10 with its ten round keys given (BatchDev::round_key, kernel parameters, so
+// the key schedule costs no instruction per round).
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const uint2* rk) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ rk[i].x, lo1, hi0 ^ c.w ^ rk[i].y, lo0);
   }
-  __device__ __forceinline__ uint32_t next() {
-    if (avail == 0) {
-      const uint4 o = philox4x32_10(make_uint4(c, j, v, s), key);
-      ++c;
-      w0 = o.x; w1 = o.y; w2 = o.z; w3 = o.w;
-      avail = 4;
-    }
-    const uint32_t r = w0;
-    w0 = w1; w1 = w2; w2 = w3;
-    --avail;
-    return r;
-  }
-};
+  return c;
+}
 
 // omega_v = ceil(RN64(r * C)); W_v = rint((r / omega_v) * 2^63)
 __device__ __noinline__ unsigned long long walks_exact(double r, double C) {
@@ -286,142 +274,6 @@ __device__ __forceinline__ unsigned long long warp_find_entry(const unsigned lon
   return lo + (unsigned long long)(31 - __clz(bal));
 }
 
-// Walk schedule: the flat walk range is cut into chunks of kChunk walks and chunk c
-// goes to warp c mod (number of warps), so the walks in flight at any time are a
-// narrow window of the source-major walk space and their end tallies stay in L2.
-// Per chunk the warp first maps every walk to its residual entry (into shared
-// memory, relative to the chunk's first entry), then each lane runs walks as a state
-// machine (one move or one walk end per loop iteration), taking the chunk's next
-// unstarted walk whenever its walk ends: walk lengths are geometric, and with a fixed
-// share of walks per lane the warp would wait for its longest share.
-template <int kMinBlocks>
-__global__ void __launch_bounds__(kWalkThreads, kMinBlocks) k_walks(GraphDev g, BatchDev b) {
-  __shared__ uint16_t smap[kWalkWarps][kChunk];
-  if (*b.err) return;
-  const unsigned long long W = b.totals[1];
-  const unsigned long long nR = b.totals[0];
-  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
-  const unsigned long long nchunks = (W + kChunk - 1) / kChunk;
-  const unsigned long long* off = b.wr_offset;
-  const uint2 key = make_uint2((uint32_t)b.seed, (uint32_t)(b.seed >> 32));
-  const uint32_t t_alpha = b.alpha_threshold;
-  unsigned long long steps_here = 0;  // moves of this lane's walks of source `cur_slot`
-  uint32_t cur_slot = 0xFFFFFFFFu;
-  bool capped = false;
-
-  for (unsigned long long c = warp; c < nchunks; c += nwarps) {
-    const unsigned long long cbeg = c * kChunk;
-    const uint32_t cnt = (uint32_t)min((unsigned long long)kChunk, W - cbeg);
-    const unsigned long long idx0 = warp_find_entry(off, nR, cbeg);
-    // map walk cbeg + i -> entry idx0 + smap[i], 32 walks at a time
-    unsigned long long idxw = idx0;
-    for (uint32_t rb = 0; rb < cnt; rb += 32) {
-      const unsigned long long gw = cbeg + rb + lane;
-      const unsigned long long o = idxw + lane < nR ? off[idxw + lane] : ~0ull;
-      int lo = 0, hi = 31;  // largest j with off[idxw + j] <= gw
-#pragma unroll
-      for (int s = 0; s < 5; ++s) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__shfl_sync(kFull, o, mid) <= gw) lo = mid; else hi = mid - 1;
-      }
-      const unsigned long long mine = idxw + (unsigned long long)lo;
-      smap[wid][rb + lane] = (uint16_t)(mine - idx0);
-      idxw = __shfl_sync(kFull, mine, 31);
-    }
-    __syncwarp();
-
-    // walks are handed to lanes in order as lanes finish (a warp-uniform counter), so
-    // no lane idles while the chunk has unstarted walks
-    uint32_t next_walk = 32;  // warp-uniform
-    uint32_t i = lane;
-    bool have = i < cnt;
-    WalkStream rng;
-    rng.key = key;
-    rng.avail = 0;
-    uint32_t x = 0, slot = 0, steps = 0;
-    unsigned long long wgt = 0;
-    bool forced = b.zero_hop;  // a pruned walk first moves without a stop test
-    if (have) {
-      const unsigned long long idx = idx0 + smap[wid][i];
-      const unsigned long long entry = b.wr_entry[idx];
-      slot = (uint32_t)(entry >> 32);
-      x = (uint32_t)entry;
-      rng.reset((uint32_t)(cbeg + i - off[idx]), x, (uint32_t)b.sources[slot]);
-      wgt = b.wr_weight[idx];
-      steps = 0;
-    }
-    for (;;) {
-      // one step of every lane: a stop test, then either a walk end or a move
-      bool stop = false;
-      if (have && !forced) stop = rng.next() < t_alpha;
-      const uint32_t stops = __ballot_sync(kFull, stop);
-      if (stop) {
-        // the walk stops at x (Section 2.1): count it and add its weight (Alg. 2), or
-        // record its end in a walk index (Section 3.3)
-        if (b.walk_dest) {
-          b.walk_dest[cbeg + i] = x;
-        } else {
-          Tally* t = b.tally + (unsigned long long)slot * (unsigned long long)g.n + x;
-          if (b.want_count) atomicAdd(&t->cnt, 1u);
-          atomicAdd(&t->acc, wgt);
-        }
-        if (slot != cur_slot) {
-          if (steps_here) atomicAdd(&b.stats[cur_slot].walk_steps, steps_here);
-          steps_here = 0;
-          cur_slot = slot;
-        }
-        steps_here += steps;
-        i = next_walk + (uint32_t)__popc(stops & ((1u << lane) - 1u));
-        have = i < cnt;
-        if (have) {
-          const unsigned long long idx = idx0 + smap[wid][i];
-          const unsigned long long entry = b.wr_entry[idx];
-          slot = (uint32_t)(entry >> 32);
-          x = (uint32_t)entry;
-          rng.reset((uint32_t)(cbeg + i - off[idx]), x, (uint32_t)b.sources[slot]);
-          wgt = b.wr_weight[idx];
-          steps = 0;
-          forced = b.zero_hop;
-        }
-      } else if (have) {
-        forced = false;
-        if (steps >= kMaxSteps) {
-          capped = true;
-          have = false;
-        } else {
-          const uint32_t rb0 = g.row[x];
-          const uint32_t d = g.row[x + 1] - rb0;
-          unsigned long long m = (unsigned long long)rng.next() * d;
-          uint32_t low = (uint32_t)m;
-          if (low < d) {
-            const uint32_t reject_below = (0u - d) % d;
-            // each retry happens with probability < d / 2^32; 64 in a row never occur
-            for (int tries = 0; low < reject_below && tries < 64; ++tries) {
-              m = (unsigned long long)rng.next() * d;
-              low = (uint32_t)m;
-            }
-          }
-          if (low < d && low < (0u - d) % d) {
-            capped = true;
-            have = false;
-          } else {
-            const uint32_t e = rb0 + (uint32_t)(m >> 32);
-            x = g.colbits ? packed_target(g.colp, g.colbits, e) : (uint32_t)g.col[e];
-            ++steps;
-          }
-        }
-      }
-      next_walk += (uint32_t)__popc(stops);
-      if (!__any_sync(kFull, have)) break;
-    }
-    __syncwarp();
-  }
-  if (capped) atomicOr(b.err, kErrWalkCap);
-  if (steps_here) atomicAdd(&b.stats[cur_slot].walk_steps, steps_here);
-}
-
 // Map walk cbeg + i (i < cnt) to its residual entry idx0 + smap[i], 32 walks at a time
 // (the entries' walk offsets are read coalesced, a 5-step search per walk in registers).
 __device__ __forceinline__ void map_chunk(const unsigned long long* off, unsigned long long nR,
@@ -452,16 +304,18 @@ __device__ __forceinline__ uint32_t walk_target(const GraphDev& g, uint32_t e) {
 
 constexpr uint32_t kCapped = 0xFFFFFFFFu;
 
-// The rest of a walk after the first try of a neighbour draw was rejected (Lemire's
-// method rejects a try with probability below d / 2^32): the walk's words are taken one
-// at a time from word `pos` of the block `blk` (the next block to generate is `cb`), first
-// for the retries of the move at x (row offset rb, degree d), then for the stop tests and
-// moves that follow, exactly in stream order.  Returns the end node, or kCapped when the
-// walk reaches the step cap (or, never in practice, 64 rejected tries in a row).
+// The rest of a walk whose neighbour draw at x (row offset rb, degree d) came out with
+// low word below d on its first try, m0 (Lemire's method then rejects the try when the low
+// word is below 2^32 mod d, probability below d / 2^32): the try is accepted or retried,
+// then the walk goes on with the words taken one at a time from word `pos` of the block
+// `blk` (the next block to generate is `cb`), stop tests and moves in stream order.
+// Returns the end node, or kCapped when the walk reaches the step cap (or, never in
+// practice, 64 rejected tries in a row).
 __device__ __forceinline__ uint32_t walk_rest(const GraphDev& g, uint4 blk, int pos, uint32_t cb,
-                                           uint32_t j, uint32_t v, uint32_t s, uint2 key,
-                                           uint32_t t_alpha, uint32_t x, uint32_t rb, uint32_t d,
-                                           uint32_t* steps) {
+                                              uint32_t j, uint32_t v, uint32_t s, uint2 key,
+                                              uint32_t t_alpha, uint32_t x, uint32_t rb,
+                                              uint32_t d, unsigned long long m0,
+                                              uint32_t* steps) {
   auto next = [&]() -> uint32_t {
     if (pos == 4) {
       blk = philox4x32_10(make_uint4(cb, j, v, s), key);
@@ -472,59 +326,188 @@ __device__ __forceinline__ uint32_t walk_rest(const GraphDev& g, uint4 blk, int 
     ++pos;
     return w;
   };
-  bool retry = true;  // the move at x still needs an accepted try
+  unsigned long long m = m0;
+  bool first = true;  // the move at x has its first try in m0
   for (;;) {
-    if (!retry) {
+    if (!first) {
       if (next() < t_alpha) return x;
       if (*steps >= kMaxSteps) return kCapped;
       const uint2 r = g.rd[x];
       rb = r.x;
       d = r.y;
-    }
-    unsigned long long m = (unsigned long long)next() * d;
-    uint32_t low = (uint32_t)m;
-    const uint32_t reject_below = (0u - d) % d;
-    int tries = 0;
-    while (low < reject_below) {
-      if (++tries > 64) return kCapped;
       m = (unsigned long long)next() * d;
-      low = (uint32_t)m;
     }
-    retry = false;
+    first = false;
+    uint32_t low = (uint32_t)m;
+    if (low < d) {
+      const uint32_t reject_below = (0u - d) % d;
+      int tries = 0;
+      while (low < reject_below) {
+        if (++tries > 64) return kCapped;
+        m = (unsigned long long)next() * d;
+        low = (uint32_t)m;
+      }
+    }
     x = walk_target(g, rb + (uint32_t)(m >> 32));
     ++*steps;
   }
 }
 
-// One move of a walk at x with the word u, on the fast path: returns false when the try
-// is rejected (the walk then finishes in walk_rest) and leaves rb, d for it.
+// One move of a walk at x with the word u, on the fast path: false when the low word of
+// the product is below d (a try Lemire's method may reject; walk_rest decides it, with
+// rb, d and m left for it), else x becomes the chosen out-neighbour.
 __device__ __forceinline__ bool fast_move(const GraphDev& g, uint32_t u, uint32_t& x,
-                                          uint32_t& rb, uint32_t& d) {
+                                          uint32_t& rb, uint32_t& d, unsigned long long& m) {
   const uint2 r = g.rd[x];
   rb = r.x;
   d = r.y;
-  const unsigned long long m = (unsigned long long)u * d;
-  const uint32_t low = (uint32_t)m;
-  if (low < d && low < (0u - d) % d) return false;
+  m = (unsigned long long)u * d;
+  if ((uint32_t)m < d) return false;
   x = walk_target(g, rb + (uint32_t)(m >> 32));
   return true;
 }
 
-// The walk kernel.  Walks are scheduled as in k_walks (chunks of kChunk walks round-robin
-// over the warps, a shared-memory map from walk to residual entry, a lane taking the
-// chunk's next unstarted walk when its walk ends), but one loop iteration consumes exactly
-// one Philox block of a lane's walk: the words of block c are, in stream order, a stop
-// test and a move, then another stop test and move (plain walks: T M T M), or a move and a
-// stop test twice (zero-hop walks, whose first move has no stop test: M T M T).  So every
-// lane with a walk evaluates its Philox block in the same iteration, and the 10-round
-// block, most of a walk's arithmetic, runs on full warps.  A walk that stops inside a
-// block leaves the block's remaining words unused, as its stream definition does.  A
-// rejected neighbour try (probability below d / 2^32) moves the walk off this block
-// alignment: walk_rest then finishes it word by word.  Walk ends of a warp that fall on the
-// same tally with the same weight are summed before one atomic (kAggregate).
-template <int kMinBlocks, bool kZeroHop, bool kAggregate>
-__global__ void __launch_bounds__(kWalkThreads, kMinBlocks) k_walks_blk(GraphDev g, BatchDev b) {
+// The first kStartCache residual entries of a warp's chunk, staged in shared memory when
+// the chunk starts (one coalesced load per lane), so that a lane starting a walk of one of
+// them reads its data there instead of making two dependent global loads.
+constexpr int kStartCache = 32;
+struct StartCache {
+  unsigned long long off[kStartCache];
+  unsigned long long wgt[kStartCache];
+  uint32_t v[kStartCache];
+  uint32_t s[kStartCache];
+  uint32_t slot[kStartCache];
+};
+
+__device__ __forceinline__ void fill_start_cache(const BatchDev& b, unsigned long long idx0,
+                                                 unsigned long long nR, StartCache& sc) {
+  const uint32_t lane = threadIdx.x & 31;
+  const unsigned long long idx = idx0 + lane;
+  if (idx < nR) {
+    const unsigned long long entry = b.wr_entry[idx];
+    const uint32_t slot = (uint32_t)(entry >> 32);
+    sc.off[lane] = b.wr_offset[idx];
+    sc.wgt[lane] = b.wr_weight[idx];
+    sc.v[lane] = (uint32_t)entry;
+    sc.slot[lane] = slot;
+    sc.s[lane] = (uint32_t)b.sources[slot];
+  }
+  __syncwarp();
+}
+
+// Per-walk state of the walk kernels.
+struct Walk {
+  uint32_t x, v, j, s, slot, steps, cb, i;
+  unsigned long long wgt;
+  bool have;
+};
+
+// Start walk w.i of the chunk (residual entry idx0 + smap[w.i]).
+__device__ __forceinline__ void start_walk(const BatchDev& b, const unsigned long long* off,
+                                           unsigned long long cbeg, unsigned long long idx0,
+                                           const uint16_t* smap, const StartCache& sc, Walk& w) {
+  const uint32_t e = smap[w.i];
+  if (e < (uint32_t)kStartCache) {
+    w.slot = sc.slot[e];
+    w.v = sc.v[e];
+    w.s = sc.s[e];
+    w.wgt = sc.wgt[e];
+    w.j = (uint32_t)(cbeg + w.i - sc.off[e]);
+  } else {
+    const unsigned long long idx = idx0 + e;
+    const unsigned long long entry = b.wr_entry[idx];
+    w.slot = (uint32_t)(entry >> 32);
+    w.v = (uint32_t)entry;
+    w.j = (uint32_t)(cbeg + w.i - off[idx]);
+    w.s = (uint32_t)b.sources[w.slot];
+    w.wgt = b.wr_weight[idx];
+  }
+  w.x = w.v;
+  w.steps = 0;
+  w.cb = 0;
+}
+
+// One iteration of a walk on its Philox block o (block index w.cb - 1): plain walks take
+// the words as stop test, move, stop test, move; zero-hop walks as move, stop test, move,
+// stop test (the first move of a zero-hop walk has no stop test).  A rejected neighbour try
+// (probability below d / 2^32) moves the walk off this block alignment: walk_rest then
+// finishes it word by word.  Returns true when the walk stopped (at w.x); sets w.have =
+// false and capped when it ran into the step cap.
+template <bool kZeroHop>
+__device__ __forceinline__ bool walk_block(const GraphDev& g, uint4 o, uint2 key, uint32_t t_alpha,
+                                           Walk& w, bool& capped) {
+  bool stop = false;
+  uint32_t rb = 0, d = 0;
+  unsigned long long m = 0;
+  int rejected = -1;  // word index of a try that walk_rest has to decide
+  const uint32_t u0 = kZeroHop ? 0u : o.x, mv0 = kZeroHop ? o.x : o.y;
+  const uint32_t t1 = kZeroHop ? o.y : o.z, mv1 = kZeroHop ? o.z : o.w;
+  if (!kZeroHop) stop = u0 < t_alpha;
+  if (!stop) {
+    if (w.steps >= kMaxSteps) { capped = true; w.have = false; return false; }
+    if (fast_move(g, mv0, w.x, rb, d, m)) {
+      ++w.steps;
+      stop = t1 < t_alpha;
+      if (!stop) {
+        if (w.steps >= kMaxSteps) { capped = true; w.have = false; return false; }
+        if (fast_move(g, mv1, w.x, rb, d, m)) {
+          ++w.steps;
+          if (kZeroHop) stop = o.w < t_alpha;
+        } else {
+          rejected = kZeroHop ? 2 : 3;
+        }
+      }
+    } else {
+      rejected = kZeroHop ? 0 : 1;
+    }
+  }
+  if (rejected >= 0) {  // rare: decide the try and finish the walk word by word
+    const uint32_t end = walk_rest(g, o, rejected + 1, w.cb, w.j, w.v, w.s, key, t_alpha, w.x,
+                                   rb, d, m, &w.steps);
+    if (end == kCapped) { capped = true; w.have = false; return false; }
+    w.x = end;
+    stop = true;
+  }
+  return stop;
+}
+
+// The end of this lane's walk w: tally it (or store it in a walk index) and count its
+// moves for its source.
+__device__ __forceinline__ void finish_walk(const BatchDev& b, unsigned long long n,
+                                            unsigned long long cbeg, const Walk& w,
+                                            unsigned long long& steps_here, uint32_t& cur_slot) {
+  // the walk stops at x (Section 2.1): count it and add its weight (Alg. 2), or record
+  // its end in a walk index (Section 3.3)
+  if (b.walk_dest) {
+    b.walk_dest[cbeg + w.i] = w.x;
+  } else {
+    Tally* t = b.tally + (unsigned long long)w.slot * n + w.x;
+    if (b.want_count) atomicAdd(&t->cnt, 1u);
+    atomicAdd(&t->acc, w.wgt);
+  }
+  if (w.slot != cur_slot) {
+    if (steps_here) atomicAdd(&b.stats[cur_slot].walk_steps, steps_here);
+    steps_here = 0;
+    cur_slot = w.slot;
+  }
+  steps_here += w.steps;
+}
+
+// The walk kernel.  The flat walk range is cut into chunks of kChunk walks and chunk c goes
+// to warp c mod (number of warps), so the walks in flight at any time are a narrow window
+// of the source-major walk space and their end tallies stay in L2.  Per chunk the warp maps
+// every walk to its residual entry (map_chunk) and stages the chunk's first entries
+// (fill_start_cache); each lane runs one walk and takes the chunk's next unstarted walk
+// when its walk ends (walk lengths are geometric: with a fixed share of walks per lane a
+// warp would wait for its longest share).  One loop iteration consumes exactly one Philox
+// block of a lane's walk (walk_block), so every lane with a walk evaluates its Philox block
+// in the same iteration and the ten rounds, most of a walk's arithmetic, run on full warps;
+// a walk that stops inside a block leaves the block's remaining words unused, as its stream
+// definition does.
+template <int kMinBlocks, bool kZeroHop>
+__global__ void __launch_bounds__(kWalkThreads, kMinBlocks) k_walks(GraphDev g, BatchDev b) {
   __shared__ uint16_t smap[kWalkWarps][kChunk];
+  __shared__ StartCache scache[kWalkWarps];
   if (*b.err) return;
   const unsigned long long W = b.totals[1];
   const unsigned long long nR = b.totals[0];
@@ -537,6 +520,7 @@ __global__ void __launch_bounds__(kWalkThreads, kMinBlocks) k_walks_blk(GraphDev
   const unsigned long long n = (unsigned long long)g.n;
   const uint2 key = make_uint2((uint32_t)b.seed, (uint32_t)(b.seed >> 32));
   const uint32_t t_alpha = b.alpha_threshold;
+  StartCache& sc = scache[wid];
   unsigned long long steps_here = 0;  // moves of this lane's walks of source `cur_slot`
   uint32_t cur_slot = 0xFFFFFFFFu;
   bool capped = false;
@@ -546,95 +530,30 @@ __global__ void __launch_bounds__(kWalkThreads, kMinBlocks) k_walks_blk(GraphDev
     const uint32_t cnt = (uint32_t)min((unsigned long long)kChunk, W - cbeg);
     const unsigned long long idx0 = warp_find_entry(off, nR, cbeg);
     map_chunk(off, nR, cbeg, cnt, idx0, smap[wid]);
+    fill_start_cache(b, idx0, nR, sc);
 
     uint32_t next_walk = 32;  // warp-uniform: the chunk's next unstarted walk
-    uint32_t i = lane;
-    bool have = i < cnt;
-    uint32_t x = 0, v = 0, j = 0, s = 0, slot = 0, steps = 0, cb = 0;
-    unsigned long long wgt = 0;
-    auto start = [&]() {
-      const unsigned long long idx = idx0 + smap[wid][i];
-      const unsigned long long entry = b.wr_entry[idx];
-      slot = (uint32_t)(entry >> 32);
-      v = (uint32_t)entry;
-      x = v;
-      j = (uint32_t)(cbeg + i - off[idx]);
-      s = (uint32_t)b.sources[slot];
-      wgt = b.wr_weight[idx];
-      steps = 0;
-      cb = 0;
-    };
-    if (have) start();
+    Walk w;
+    w.i = lane;
+    w.have = w.i < cnt;
+    if (w.have) start_walk(b, off, cbeg, idx0, smap[wid], sc, w);
     for (;;) {
       bool stop = false;
-      if (have) {
-        const uint4 o = philox4x32_10(make_uint4(cb, j, v, s), key);
-        ++cb;
-        uint32_t rb = 0, d = 0;
-        int rejected = -1;  // word index of a rejected try
-        if (!kZeroHop) {
-          stop = o.x < t_alpha;
-          if (!stop) {
-            if (steps >= kMaxSteps) { capped = true; have = false; }
-            else if (fast_move(g, o.y, x, rb, d)) { ++steps; stop = o.z < t_alpha; }
-            else rejected = 1;
-          }
-          if (have && !stop && rejected < 0) {
-            if (steps >= kMaxSteps) { capped = true; have = false; }
-            else if (fast_move(g, o.w, x, rb, d)) ++steps;
-            else rejected = 3;
-          }
-        } else {
-          if (steps >= kMaxSteps) { capped = true; have = false; }
-          else if (fast_move(g, o.x, x, rb, d)) { ++steps; stop = o.y < t_alpha; }
-          else rejected = 0;
-          if (have && !stop && rejected < 0) {
-            if (steps >= kMaxSteps) { capped = true; have = false; }
-            else if (fast_move(g, o.z, x, rb, d)) { ++steps; stop = o.w < t_alpha; }
-            else rejected = 2;
-          }
-        }
-        if (rejected >= 0) {  // rare: finish the walk word by word
-          const uint32_t end = walk_rest(g, o, rejected + 1, cb, j, v, s, key, t_alpha, x, rb, d,
-                                         &steps);
-          if (end == kCapped) { capped = true; have = false; }
-          else { x = end; stop = true; }
-        }
+      if (w.have) {
+        const uint4 o = philox_rk(make_uint4(w.cb, w.j, w.v, w.s), b.round_key);
+        ++w.cb;
+        stop = walk_block<kZeroHop>(g, o, key, t_alpha, w, capped);
       }
-      const bool ended = have && stop;
+      const bool ended = w.have && stop;
       const uint32_t ends = __ballot_sync(kFull, ended);
       if (ended) {
-        // the walk stops at x (Section 2.1): count it and add its weight (Alg. 2), or
-        // record its end in a walk index (Section 3.3)
-        if (b.walk_dest) {
-          b.walk_dest[cbeg + i] = x;
-        } else {
-          Tally* t = b.tally + (unsigned long long)slot * n + x;
-          if (kAggregate) {
-            const unsigned grp = __match_any_sync(ends, (unsigned long long)t) &
-                                 __match_any_sync(ends, wgt);
-            if ((grp & lt_mask) == 0) {  // the group's lowest lane adds for all of it
-              const uint32_t k = (uint32_t)__popc(grp);
-              if (b.want_count) atomicAdd(&t->cnt, k);
-              atomicAdd(&t->acc, wgt * (unsigned long long)k);
-            }
-          } else {
-            if (b.want_count) atomicAdd(&t->cnt, 1u);
-            atomicAdd(&t->acc, wgt);
-          }
-        }
-        if (slot != cur_slot) {
-          if (steps_here) atomicAdd(&b.stats[cur_slot].walk_steps, steps_here);
-          steps_here = 0;
-          cur_slot = slot;
-        }
-        steps_here += steps;
-        i = next_walk + (uint32_t)__popc(ends & lt_mask);
-        have = i < cnt;
-        if (have) start();
+        finish_walk(b, n, cbeg, w, steps_here, cur_slot);
+        w.i = next_walk + (uint32_t)__popc(ends & lt_mask);
+        w.have = w.i < cnt;
+        if (w.have) start_walk(b, off, cbeg, idx0, smap[wid], sc, w);
       }
       next_walk += (uint32_t)__popc(ends);
-      if (!__any_sync(kFull, have)) break;
+      if (!__any_sync(kFull, w.have)) break;
     }
     __syncwarp();
   }
@@ -741,47 +660,28 @@ cudaError_t launch_residuals(const GraphDev& g, const BatchDev& b, cudaStream_t 
   return cudaGetLastError();
 }
 
-// Walk kernel instances for 4, 5 or 6 resident blocks of 256 threads per SM (the
-// register budget the compiler gets); b.walk_blocks picks one (launch shape only).
-template <int kMinBlocks>
+// Walk kernel instances for 3, 4 or 5 resident blocks of 256 threads per SM (the register
+// budget the compiler gets); b.walk_blocks picks one (launch shape only).
+template <int kMinBlocks, bool kZeroHop>
 cudaError_t launch_walks_t(const GraphDev& g, const BatchDev& b, int num_sms, cudaStream_t st) {
-  const int per_sm = resident_blocks((const void*)k_walks<kMinBlocks>, kWalkThreads);
+  const int per_sm = resident_blocks((const void*)k_walks<kMinBlocks, kZeroHop>, kWalkThreads);
   if (per_sm == 0) return cudaErrorInvalidConfiguration;
-  k_walks<kMinBlocks><<<num_sms * per_sm, kWalkThreads, 0, st>>>(g, b);
+  k_walks<kMinBlocks, kZeroHop><<<num_sms * per_sm, kWalkThreads, 0, st>>>(g, b);
   return cudaGetLastError();
 }
 
-template <int kMinBlocks, bool kZeroHop, bool kAggregate>
-cudaError_t launch_walks_blk_t(const GraphDev& g, const BatchDev& b, int num_sms,
-                               cudaStream_t st) {
-  const void* k = (const void*)k_walks_blk<kMinBlocks, kZeroHop, kAggregate>;
-  const int per_sm = resident_blocks(k, kWalkThreads);
-  if (per_sm == 0) return cudaErrorInvalidConfiguration;
-  k_walks_blk<kMinBlocks, kZeroHop, kAggregate><<<num_sms * per_sm, kWalkThreads, 0, st>>>(g, b);
-  return cudaGetLastError();
-}
-
-template <bool kZeroHop, bool kAggregate>
-cudaError_t launch_walks_blk(const GraphDev& g, const BatchDev& b, int num_sms, cudaStream_t st) {
+template <bool kZeroHop>
+cudaError_t launch_walks_zh(const GraphDev& g, const BatchDev& b, int num_sms, cudaStream_t st) {
   switch (b.walk_blocks) {
-    case 6: return launch_walks_blk_t<6, kZeroHop, kAggregate>(g, b, num_sms, st);
-    case 5: return launch_walks_blk_t<5, kZeroHop, kAggregate>(g, b, num_sms, st);
-    default: return launch_walks_blk_t<4, kZeroHop, kAggregate>(g, b, num_sms, st);
+    case 3: return launch_walks_t<3, kZeroHop>(g, b, num_sms, st);
+    case 5: return launch_walks_t<5, kZeroHop>(g, b, num_sms, st);
+    default: return launch_walks_t<4, kZeroHop>(g, b, num_sms, st);
   }
 }
 
 cudaError_t launch_walks(const GraphDev& g, const BatchDev& b, int num_sms, cudaStream_t st) {
-  if (b.walk_variant == 1)
-    return b.zero_hop ? launch_walks_blk<true, false>(g, b, num_sms, st)
-                      : launch_walks_blk<false, false>(g, b, num_sms, st);
-  if (b.walk_variant == 2)
-    return b.zero_hop ? launch_walks_blk<true, true>(g, b, num_sms, st)
-                      : launch_walks_blk<false, true>(g, b, num_sms, st);
-  switch (b.walk_blocks) {
-    case 6: return launch_walks_t<6>(g, b, num_sms, st);
-    case 5: return launch_walks_t<5>(g, b, num_sms, st);
-    default: return launch_walks_t<4>(g, b, num_sms, st);
-  }
+  return b.zero_hop ? launch_walks_zh<true>(g, b, num_sms, st)
+                    : launch_walks_zh<false>(g, b, num_sms, st);
 }
 
 cudaError_t launch_index_residue(const GraphDev& g, double* r, double rmax, cudaStream_t st) {

@@ -96,14 +96,21 @@ def test_push_matches_oracle(rmat14):
         assert st[i].rsum == pytest.approx(pst.rsum, abs=1e-12)
 
 
-def test_walks_and_topk_bit_exact_on_oracle_residues(rmat14):
+@pytest.mark.parametrize("walk_blocks", [3, 4, 5])
+def test_walks_and_topk_bit_exact_on_oracle_residues(rmat14, walk_blocks):
+    """Every walk kernel instance (3, 4 or 5 resident blocks per SM) consumes each walk's
+    Philox words exactly as the oracle's word-by-word walk does."""
     rp, col, g = rmat14
     n = len(rp) - 1
     sources = inputs.uniform_sources(n, 10, inputs.SOURCE_SEED)
     p = fora.Params.make(k=50, seed=inputs.WALK_SEED)
     qs = [oracle.ssppr(rp, col, s, k=50, seed=inputs.WALK_SEED) for s in sources]
     given = (np.stack([q.reserve for q in qs]), np.stack([q.residue for q in qs]))
-    ids, vals, st, out = run_debug(g, sources, p, given=given)
+    g.tune("walk_blocks", walk_blocks)
+    try:
+        ids, vals, st, out = run_debug(g, sources, p, given=given)
+    finally:
+        g.tune("walk_blocks", 3)
     for i, q in enumerate(qs):
         np.testing.assert_array_equal(out["count"][i], q.count)
         np.testing.assert_array_equal(out["acc"][i], q.acc)
@@ -306,10 +313,10 @@ def test_autotuner_and_launch_shapes_do_not_change_results(rmat14):
     p = fora.Params.make(k=50, seed=8)
     ref_ids, ref_vals, ref_st, ref = run_debug(g, sources, p)
     choice = g.autotune(sources, p)
-    assert choice["spread_width"] in (1, 2, 4, 8, 16) and choice["walk_blocks"] in (4, 5, 6)
+    assert choice["spread_width"] in (1, 2, 4, 8, 16) and choice["walk_blocks"] in (3, 4, 5)
     assert choice["pipeline"] == 1  # 12 sources: too few to split
     assert g.tuning("walk_blocks") == choice["walk_blocks"]
-    for sw, wb in [(1, 4), (16, 5), (3, 6), (choice["spread_width"], choice["walk_blocks"])]:
+    for sw, wb in [(1, 3), (16, 5), (3, 4), (choice["spread_width"], choice["walk_blocks"])]:
         g.tune("spread_width", sw)
         g.tune("walk_blocks", wb)
         ids, vals, st, out = run_debug(g, sources, p, given=(ref["reserve"], ref["residue"]))
@@ -319,9 +326,9 @@ def test_autotuner_and_launch_shapes_do_not_change_results(rmat14):
         np.testing.assert_allclose(out2["reserve"], ref["reserve"], rtol=0, atol=ATOL_PUSH)
         assert [s.pushes for s in st2] == [s.pushes for s in ref_st]
     with pytest.raises(fora.FORAError):
-        g.tune("walk_blocks", 7)
+        g.tune("walk_blocks", 6)
     g.tune("spread_width", 1)
-    g.tune("walk_blocks", 4)
+    g.tune("walk_blocks", 3)
 
 
 def test_host_driven_push_loop_matches_oracle(rmat14):
@@ -406,3 +413,29 @@ def test_pipelined_batch_equals_one_part(rmat14):
         g.tune("pipeline", 1)
     with pytest.raises(fora.FORAError):
         g.tune("pipeline", 5)
+
+
+@pytest.mark.parametrize("zero_hop", [False, True])
+def test_rejected_neighbour_draws_follow_the_word_stream(zero_hop):
+    """Lemire's method rejects a neighbour try when its low word is below 2^32 mod d, so a
+    walk whose try is rejected takes an extra word and leaves the kernel's one-block-per-
+    iteration alignment (it is finished word by word).  A hub with d = 100000 out-edges
+    (2^32 mod d = 67296) and 100000 leaves that point back to it: every second move draws
+    at the hub, about 1.6e-5 of those tries are rejected and 2.3e-5 take the careful path,
+    so the ~1.1e7 Monte-Carlo walks from the hub (r_max = 1: no push) meet both about a
+    hundred times or more.  Counts and weights must still equal the oracle's bit for bit."""
+    hub, leaves = 0, 100000
+    edges = [(hub, u) for u in range(1, leaves + 1)] + [(u, hub) for u in range(1, leaves + 1)]
+    rp, col = inputs.csr_from_edges(leaves + 1, edges)
+    g = fora.Graph(rp, col)
+    flags = fora.FORA_ZERO_HOP if zero_hop else 0
+    p = fora.Params.make(k=50, rmax=1.0, delta=1e-5, pf=1e-5, seed=99, flags=flags)
+    q = oracle.ssppr(rp, col, hub, k=50, rmax=1.0, delta=1e-5, pf=1e-5, seed=99,
+                     zero_hop=zero_hop)
+    assert q.walk.walks > 5_000_000
+    ids, vals, st, out = run_debug(g, [hub], p, given=(q.reserve[None], q.residue[None]))
+    np.testing.assert_array_equal(out["count"][0], q.count)
+    np.testing.assert_array_equal(out["acc"][0], q.acc)
+    np.testing.assert_array_equal(ids[0], q.ids)
+    assert st[0].walk_steps == q.walk.walk_steps
+    g.close()

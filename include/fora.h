@@ -374,7 +374,7 @@ int fora_threshold_debug(const double *r, const double *rmax, const uint32_t *d,
  * (grouped by source) through this many interleaved segments, so the warps in flight cover about that
  * many sources at once (wider spreads reductions on shared hub targets over more
  * addresses; narrower keeps the residue arrays in flight smaller).  "walk_blocks" (3, 4
- * or 5, default 3): resident walk blocks per SM, traded against registers per thread.
+ * or 5, default 4): resident walk blocks per SM, traded against registers per thread.
  * "push_host_loop" (0 or 1, default 0): 1 launches the push rounds from a host loop with
  * one device-to-host read per round, instead of the CUDA graph whose conditional while-node
  * runs them on the device; the kernels are the same (a profiler that cannot look inside

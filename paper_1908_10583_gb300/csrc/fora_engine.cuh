@@ -137,7 +137,7 @@ struct BatchDev {
 // Launch-shape parameters of a graph (set through fora_graph_tune or the autotuner).
 struct Tuning {
   int spread_width = 1;
-  int walk_blocks = 3;
+  int walk_blocks = 4;
   int push_host_loop = 0;  // 1: rounds launched from a host loop instead of the graph
   int pipeline = 1;        // parts of a batch run on their own streams, pushes staggered
   uint32_t max_push_rounds = kMaxPushRounds;

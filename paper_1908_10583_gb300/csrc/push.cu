@@ -141,12 +141,32 @@ __global__ void k_push_seed(GraphDev g, BatchDev b) {
   }
 }
 
+// r[base + u] += inc for the active lanes of one 32-edge slice whose lanes hold consecutive
+// CSR entries (lane order = entry order; inactive lanes only at the end).  Rows are
+// sorted, so the copies of a multi-edge (v, u) are adjacent: a run of lanes with the same
+// target from the same frontier node (`owner`) becomes one reduction of k * inc by its
+// first lane (k copies counted with multiplicity, as Alg. 1 pushes along each of them;
+// one rounding instead of k, which only reorders the FP64 sum like the atomics do).
+__device__ __forceinline__ void spread_slice(double* r, unsigned long long base, uint32_t u,
+                                             uint32_t owner, double inc, bool act) {
+  const uint32_t lane = lane_id();
+  const uint32_t pu = __shfl_up_sync(kFull, u, 1);
+  const uint32_t po = __shfl_up_sync(kFull, owner, 1);
+  const bool cont = act && lane > 0 && pu == u && po == owner;  // continues lane - 1's run
+  const uint32_t brk = __ballot_sync(kFull, !cont);              // run starts and idle lanes
+  if (act && !cont) {
+    const uint32_t above = brk & ~((2u << lane) - 1u);
+    const uint32_t k = (above ? (uint32_t)__ffs(above) - 1u : 32u) - lane;
+    atomicAdd(&r[base + u], k == 1u ? inc : __dmul_rn(inc, (double)k));
+  }
+}
+
 // Work is handed out dynamically (kGrab groups or hub items per atomic), so the warps
 // in flight always hold the next unprocessed stretch of the frontier, whatever the cost
 // of each group.
 constexpr unsigned long long kGrab = 4;
 
-__global__ void __launch_bounds__(kSpreadThreads) k_push_spread(GraphDev g, BatchDev b) {
+__global__ void __launch_bounds__(kSpreadThreads, 6) k_push_spread(GraphDev g, BatchDev b) {
   const int cur = b.ps->cur;
   const unsigned long long ngroups = b.ps->ngroups;
   const unsigned long long nh = b.ps->nhub;
@@ -195,7 +215,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_push_spread(GraphDev g, Batc
       const uint32_t total = __shfl_sync(kFull, incl, 31);
       const uint32_t excl = incl - c;
       for (uint32_t base = 0; base < total; base += 128) {
-        uint32_t u[4];
+        uint32_t u[4], own[4];
         double ik[4];
         bool act[4];
 #pragma unroll
@@ -210,12 +230,12 @@ __global__ void __launch_bounds__(kSpreadThreads) k_push_spread(GraphDev g, Batc
           const uint32_t ek = __shfl_sync(kFull, excl, lo);
           const uint32_t rbk = __shfl_sync(kFull, rb, lo);
           ik[k] = __shfl_sync(kFull, inc, lo);
+          own[k] = (uint32_t)lo;
           act[k] = e < total;
           u[k] = act[k] ? (uint32_t)g.col[rbk + (e - ek)] : 0u;
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (act[k]) atomicAdd(&b.r[base_gi + u[k]], ik[k]);
+        for (int k = 0; k < 4; ++k) spread_slice(b.r, base_gi, u[k], own[k], ik[k], act[k]);
       }
     }
   }
@@ -257,7 +277,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_push_spread(GraphDev g, Batc
       }
 #pragma unroll
       for (int k = 0; k < (int)(kHubChunk / 32); ++k)
-        if (u[k] != 0xFFFFFFFFu) atomicAdd(&b.r[gbase + u[k]], inc);
+        spread_slice(b.r, gbase, u[k], 0u, inc, u[k] != 0xFFFFFFFFu);
     }
   }
 }

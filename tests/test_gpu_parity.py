@@ -110,7 +110,7 @@ def test_walks_and_topk_bit_exact_on_oracle_residues(rmat14, walk_blocks):
     try:
         ids, vals, st, out = run_debug(g, sources, p, given=given)
     finally:
-        g.tune("walk_blocks", 3)
+        g.tune("walk_blocks", 4)
     for i, q in enumerate(qs):
         np.testing.assert_array_equal(out["count"][i], q.count)
         np.testing.assert_array_equal(out["acc"][i], q.acc)
@@ -328,7 +328,7 @@ def test_autotuner_and_launch_shapes_do_not_change_results(rmat14):
     with pytest.raises(fora.FORAError):
         g.tune("walk_blocks", 6)
     g.tune("spread_width", 1)
-    g.tune("walk_blocks", 3)
+    g.tune("walk_blocks", 4)
 
 
 def test_host_driven_push_loop_matches_oracle(rmat14):

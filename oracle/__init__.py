@@ -5,8 +5,8 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 under ``paper_1908_10583_gb300``) never calls it and shares no code with it.
 
 ``fora_oracle.c`` holds the query steps (parameters, Forward Push in
-synchronous rounds (Alg. 1), the random-walk phase of Alg. 2, estimate,
-exact top-k) in plain FP64 C; ``exact.py`` holds the ground truth (dense
+synchronous rounds (Alg. 1) and its balanced form (Alg. 3), the random-walk
+phase of Alg. 2, estimate, exact top-k) in plain FP64 C; ``exact.py`` holds the ground truth (dense
 solve and power iteration of Eq. (powerit)) in numpy/scipy.  Every function
 here is pinned by ``tests/test_oracle_*.py`` against closed forms,
 invariants, published test vectors and brute force.
@@ -78,6 +78,9 @@ def _load():
             lib.oracle_philox4x32_10.argtypes = [P, P, P]
             lib.oracle_forward_push.restype = ctypes.c_int
             lib.oracle_forward_push.argtypes = [i64, P, P, i32, dbl, dbl, P, P, P]
+            lib.oracle_forward_push_balanced.restype = ctypes.c_int
+            lib.oracle_forward_push_balanced.argtypes = [i64, P, P, i32, dbl, dbl, dbl, dbl, dbl,
+                                                         P, P, P, P]
             lib.oracle_walk_phase.restype = ctypes.c_int
             lib.oracle_walk_phase.argtypes = [i64, P, P, i32, dbl, dbl, u64, P, P, P, P]
             lib.oracle_walk_phase_zero_hop.restype = ctypes.c_int
@@ -151,6 +154,24 @@ def forward_push(row_ptr, col, s, alpha, rmax):
     if rc:
         raise OracleError(rc)
     return reserve, residue, st
+
+
+def forward_push_balanced(row_ptr, col, s, alpha, walk_scale, cost_edge, cost_push, cost_walk):
+    """Forward Push with push/walk balancing (Section 4.2, Alg. 3), synchronous rounds:
+    walk_scale is C' (C, or (1 - alpha) C with zero-hop pruning), the costs are per edge
+    push, per node push and per walk -> (reserve, residue, PushStats, final threshold)."""
+    row_ptr, col, n = _graph(row_ptr, col)
+    reserve = np.zeros(n)
+    residue = np.zeros(n)
+    st = PushStats()
+    theta = ctypes.c_double(0.0)
+    rc = _load().oracle_forward_push_balanced(n, _ptr(row_ptr), _ptr(col), int(s), alpha,
+                                              walk_scale, cost_edge, cost_push, cost_walk,
+                                              _ptr(reserve), _ptr(residue), ctypes.addressof(st),
+                                              ctypes.addressof(theta))
+    if rc:
+        raise OracleError(rc)
+    return reserve, residue, st, theta.value
 
 
 def walk_phase(row_ptr, col, s, alpha, scale, seed, residue):

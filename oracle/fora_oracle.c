@@ -197,6 +197,84 @@ int oracle_forward_push(int64_t n, const int64_t *row_ptr, const int32_t *col, i
   return ORACLE_OK;
 }
 
+/*
+ * Forward Push with push/walk balancing (Section 4.2, Alg. 3), in synchronous rounds.
+ * Alg. 3 keeps pushing while some node is above the threshold and the push cost so far,
+ * FC, is below the estimated cost of the walks that would follow, omega * rc, where
+ * omega = r_sum * C' (C' = C, or (1 - alpha) C with zero-hop pruning) and rc is the cost
+ * of one walk; it starts from r_max = 1.  Read here: the threshold theta starts at 1 and
+ * is halved whenever no node is above it (with theta = 1 nothing can be, since r <= 1 <=
+ * d_out), so the threshold falls until the cost rule stops the push.  Costs are counted,
+ * not timed: FC = cost_edge * (edge pushes) + cost_push * (node pushes), and
+ * r_sum = 1 - (sum of the alpha r(v) moved to reserves), as the mass is conserved.
+ * Each loop step: stop if FC >= (r_sum * C') * cost_walk; else take the set of nodes
+ * with r(v) > theta * d_out(v) (ascending id) and push it as one round (as
+ * oracle_forward_push does), or halve theta if the set is empty.
+ * Writes reserve[n], residue[n], the statistics and the final theta.
+ */
+int oracle_forward_push_balanced(int64_t n, const int64_t *row_ptr, const int32_t *col,
+                                 int32_t s, double alpha, double walk_scale, double cost_edge,
+                                 double cost_push, double cost_walk, double *reserve,
+                                 double *residue, oracle_push_stats *st, double *theta_out) {
+  int rc = check_graph(n, row_ptr, col);
+  if (rc) return rc;
+  if (s < 0 || s >= n || !(alpha > 0.0 && alpha < 1.0) || !(walk_scale > 0.0) ||
+      !(cost_edge >= 0.0) || !(cost_push >= 0.0) || !(cost_walk >= 0.0))
+    return ORACLE_ERR_BAD_ARG;
+  int32_t *frontier = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  double *taken = (double *)malloc(sizeof(double) * (size_t)n);
+  if (!frontier || !taken) {
+    free(frontier); free(taken);
+    return ORACLE_ERR_OOM;
+  }
+  oracle_push_stats local = {0, 0, 0, 0.0};
+  for (int64_t v = 0; v < n; ++v) { reserve[v] = 0.0; residue[v] = 0.0; }
+  residue[s] = 1.0;
+  double theta = 1.0;
+  double moved = 0.0;  /* sum of alpha * r(v) over all pushes */
+  int64_t steps = 0;
+  for (;;) {
+    const double fc = cost_edge * (double)local.edge_pushes + cost_push * (double)local.pushes;
+    const double walk_cost = ((1.0 - moved) * walk_scale) * cost_walk;
+    if (fc >= walk_cost) break;
+    if (steps++ >= ORACLE_ROUND_CAP) {
+      free(frontier); free(taken);
+      return ORACLE_ERR_PUSH_NOT_CONVERGED;
+    }
+    int64_t nf = 0;
+    for (int64_t v = 0; v < n; ++v) {
+      double d = (double)(row_ptr[v + 1] - row_ptr[v]);
+      if (residue[v] > theta * d) frontier[nf++] = (int32_t)v;
+    }
+    if (nf == 0) {
+      theta = 0.5 * theta;
+      continue;
+    }
+    local.rounds++;
+    local.pushes += nf;
+    for (int64_t i = 0; i < nf; ++i) {
+      int32_t v = frontier[i];
+      taken[i] = residue[v];
+      reserve[v] += alpha * taken[i];
+      moved += alpha * taken[i];
+      residue[v] = 0.0;
+    }
+    for (int64_t i = 0; i < nf; ++i) {
+      int32_t v = frontier[i];
+      int64_t d = row_ptr[v + 1] - row_ptr[v];
+      double inc = ((1.0 - alpha) * taken[i]) / (double)d;
+      for (int64_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) residue[col[e]] += inc;
+      local.edge_pushes += d;
+    }
+  }
+  for (int64_t v = 0; v < n; ++v) local.rsum += residue[v];
+  free(frontier);
+  free(taken);
+  if (st) *st = local;
+  if (theta_out) *theta_out = theta;
+  return ORACLE_OK;
+}
+
 /* ---------------------------------------------------------- walk phase */
 
 typedef struct {

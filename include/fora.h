@@ -186,6 +186,37 @@ int fora_ssppr_batch_rmax(fora_graph *g, const fora_params *params, const int32_
                           fora_stats *stats, void *stream);
 
 /*
+ * Push/walk balancing of Section 4.2 (Alg. 3): the push of each source stops, before a
+ * round, as soon as its cost so far reaches the estimated cost of the walks that would
+ * follow: FC = edge_push * (edge pushes) + push * (node pushes) against
+ * (r_sum * C') * walk, with r_sum the residue left (1 minus the mass moved to reserves),
+ * C' = C = omega / r_sum of Alg. 2 ((1 - alpha) C with FORA_ZERO_HOP) and `walk` the cost
+ * of one walk.  The costs are in any one unit (for instance milliseconds measured on this
+ * device); all three are finite and >= 0.  Alg. 3 starts from r_max = 1, under which no
+ * node is above the threshold (r <= 1 <= d_out); this library reads it as a threshold
+ * theta that starts at 1 and halves whenever no node of the source is above it, so the
+ * threshold falls until the cost rule stops the push.  Pushes are otherwise the
+ * synchronous rounds of Alg. 1, and the walks and estimate are those of Alg. 2 on the
+ * residues the push leaves (the accuracy guarantee holds for any residues, Lemma
+ * (layerppr-conc)).
+ */
+typedef struct {
+  double edge_push; /* cost of pushing along one edge (with multiplicity) */
+  double push;      /* cost of taking one node */
+  double walk;      /* cost of one random walk */
+} fora_balance;
+
+/*
+ * fora_ssppr_batch with the balanced push (fora_balance) per source instead of a fixed
+ * r_max (params->rmax is not used); stats[i].rmax reports the final threshold theta of
+ * source i.  FORA_USE_INDEX is refused (FORA_ERR_BAD_ARG: theta is not bounded by an
+ * index's r_max).  Same outputs, conventions and errors as fora_ssppr_batch.
+ */
+int fora_ssppr_batch_balanced(fora_graph *g, const fora_params *params, const fora_balance *costs,
+                              const int32_t *sources, int32_t nsrc, int32_t *out_ids,
+                              double *out_vals, fora_stats *stats, void *stream);
+
+/*
  * Top-k FORA (Alg. 5, Section 5.2) for nsrc sources: for delta = 1/k, 1/(2k), ...
  * and finally 1/n, run the query with eps' = eps/2, failure probability
  * p_f' = p_f / (n log2(n/k)) (log2 taken as at least 1) and r_max by the rule for these
@@ -313,6 +344,8 @@ typedef struct {
   uint32_t *count;   /* walks ending at each node */
   uint64_t *acc;     /* fixed-point walk weight ending at each node (2^-63 units) */
   double *estimate;  /* pi_hat */
+  const fora_balance *balance; /* NULL, or the balanced push of Alg. 3 with these costs
+                                  (host struct; params->rmax is then not used) */
 } fora_debug_io;
 
 #define FORA_DBG_GIVEN_PUSH 0x1u /* skip the push; take reserve/residue from dbg (device) */

@@ -79,10 +79,16 @@ class RequestInfo(ctypes.Structure):
                 ("lane", ctypes.c_int32), ("stats", Stats)]
 
 
+class Balance(ctypes.Structure):
+    """fora_balance: costs of one edge push, one node push and one walk (Alg. 3)."""
+    _fields_ = [("edge_push", ctypes.c_double), ("push", ctypes.c_double),
+                ("walk", ctypes.c_double)]
+
+
 class DebugIO(ctypes.Structure):
     _fields_ = [("reserve", ctypes.c_void_p), ("residue", ctypes.c_void_p),
                 ("count", ctypes.c_void_p), ("acc", ctypes.c_void_p),
-                ("estimate", ctypes.c_void_p)]
+                ("estimate", ctypes.c_void_p), ("balance", ctypes.c_void_p)]
 
 
 def lib_path() -> str:
@@ -116,6 +122,9 @@ def load():
         L.fora_ssppr_batch_debug.restype = I
         L.fora_ssppr_batch_debug.argtypes = [P, ctypes.POINTER(Params), P, i32, P, P, P,
                                              ctypes.POINTER(DebugIO), u32, P]
+        L.fora_ssppr_batch_balanced.restype = I
+        L.fora_ssppr_batch_balanced.argtypes = [P, ctypes.POINTER(Params), ctypes.POINTER(Balance),
+                                                P, i32, P, P, P, P]
         L.fora_ssppr_batch_rmax.restype = I
         L.fora_ssppr_batch_rmax.argtypes = [P, ctypes.POINTER(Params), P, P, i32, P, P, P, P]
         L.fora_topk_ssppr_batch.restype = I
@@ -344,6 +353,26 @@ class Graph:
                                             ctypes.addressof(st), _stream_ptr(stream)))
         return out_ids, out_vals, list(st)
 
+    def ssppr_batch_balanced(self, sources, params: Params, costs, out_ids=None, out_vals=None,
+                             stream=None):
+        """Batched query with the balanced push of Alg. 3; costs = (edge_push, push, walk)."""
+        src = np.ascontiguousarray(sources, dtype=np.int32)
+        nsrc, k = len(src), params.k
+        p = Params.from_buffer_copy(params)
+        if out_ids is not None:
+            p.flags |= FORA_OUT_DEVICE
+        else:
+            p.flags &= ~FORA_OUT_DEVICE
+            out_ids = np.zeros((nsrc, k), dtype=np.int32)
+            out_vals = np.zeros((nsrc, k), dtype=np.float64)
+        st = (Stats * nsrc)()
+        bal = Balance(*[float(c) for c in costs])
+        _check(load().fora_ssppr_batch_balanced(self._h, ctypes.byref(p), ctypes.byref(bal),
+                                                src.ctypes.data, nsrc, _ptr(out_ids),
+                                                _ptr(out_vals), ctypes.addressof(st),
+                                                _stream_ptr(stream)))
+        return out_ids, out_vals, list(st)
+
     def features(self, sources, params: Params):
         """Per-source features of the learned r_max (fora_source_features) -> [nsrc, 16]."""
         src = np.ascontiguousarray(sources, dtype=np.int32)
@@ -402,9 +431,10 @@ class Graph:
         return out_ids, out_vals
 
     def ssppr_batch_debug(self, sources, params: Params, dbg: dict, given_push=False,
-                          stream=None):
+                          stream=None, balance=None):
         """Batched query exposing intermediate arrays.  dbg maps any of reserve, residue,
-        count, acc, estimate to torch CUDA tensors of shape [nsrc, n]."""
+        count, acc, estimate to torch CUDA tensors of shape [nsrc, n]; balance = (edge_push,
+        push, walk) selects the balanced push of Alg. 3."""
         src = np.ascontiguousarray(sources, dtype=np.int32)
         nsrc, k = len(src), params.k
         p = Params.from_buffer_copy(params)
@@ -412,7 +442,9 @@ class Graph:
         ids = np.zeros((nsrc, k), dtype=np.int32)
         vals = np.zeros((nsrc, k), dtype=np.float64)
         st = (Stats * nsrc)()
-        io = DebugIO(*[_ptr(dbg.get(f)) for f, _ in DebugIO._fields_])
+        bal = Balance(*[float(c) for c in balance]) if balance is not None else None
+        io = DebugIO(*[_ptr(dbg.get(f)) for f, _ in DebugIO._fields_[:5]],
+                     ctypes.addressof(bal) if bal is not None else None)
         _check(load().fora_ssppr_batch_debug(self._h, ctypes.byref(p), src.ctypes.data, nsrc,
                                              ids.ctypes.data, vals.ctypes.data, ctypes.addressof(st),
                                              ctypes.byref(io),

@@ -115,6 +115,7 @@ fora::WorkspaceSizes fora::workspace_sizes(int64_t n, uint64_t hub_chunks, int n
   z.sources = S * sizeof(int32_t);
   z.rmax = S * sizeof(double);
   z.stats = S * sizeof(SlotStats);
+  z.stopped = S * sizeof(uint32_t);
   z.blk = 2 * (size_t)kMaxResidualGrid * sizeof(unsigned long long);
   z.topk = topk_scratch_bytes(nsrc);
   z.feat = S * FORA_NUM_FEATURES * sizeof(float);
@@ -127,8 +128,8 @@ fora::WorkspaceSizes fora::workspace_sizes(int64_t n, uint64_t hub_chunks, int n
 
 size_t fora::WorkspaceSizes::total() const {
   return r + res + tally + 2 * q + fa + 2 * hub + small + work + alist + slot_cnt + pre + ps +
-         err + sources + rmax + stats + blk + topk + feat + pred + rmax_learned + out_ids +
-         out_vals;
+         err + sources + rmax + stats + stopped + blk + topk + feat + pred + rmax_learned +
+         out_ids + out_vals;
 }
 
 namespace {
@@ -166,6 +167,7 @@ int ensure_workspace(fora_graph* g, Workspace* w, int nsrc) {
   CUDA_TRY(dalloc(&w->sources, z.sources));
   CUDA_TRY(dalloc(&w->rmax, z.rmax));
   CUDA_TRY(dalloc(&w->stats, z.stats));
+  CUDA_TRY(dalloc(&w->stopped, z.stopped));
   CUDA_TRY(dalloc(&w->blk, z.blk));
   CUDA_TRY(dalloc(&w->topk_scratch, z.topk));
   CUDA_TRY(dalloc(&w->feat, z.feat));
@@ -241,7 +243,17 @@ namespace {
 // The instantiated graph is kept in the workspace and rebuilt when the workspace, the
 // number of sources, alpha or the launch shape change.
 int push_loop_graph(fora_graph* g, Workspace* w, const GraphDev& gd, const BatchDev& b) {
-  const PushGraphKey key{w->generation, b.nsrc, b.alpha, b.spread_width, b.max_rounds};
+  PushGraphKey key;
+  key.generation = w->generation;
+  key.nsrc = b.nsrc;
+  key.alpha = b.alpha;
+  key.spread_width = b.spread_width;
+  key.max_rounds = b.max_rounds;
+  key.balance = b.balance;
+  key.bal[0] = b.bal_scale;
+  key.bal[1] = b.cost_edge;
+  key.bal[2] = b.cost_push;
+  key.bal[3] = b.cost_walk;
   if (w->push_exec && key == w->push_key) return FORA_OK;
   if (w->push_exec) {
     cudaGraphExecDestroy(w->push_exec);
@@ -291,7 +303,8 @@ int fora::reserve_workspace(fora_graph* g, Workspace* w, int nsrc) {
 int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
                        const int32_t* sources, int nsrc, int32_t* out_ids, double* out_vals,
                        fora_stats* st, const fora_debug_io* dbg, uint32_t dbg_flags,
-                       cudaStream_t stream, RmaxSource rsrc, const PipeHook* hook) {
+                       cudaStream_t stream, RmaxSource rsrc, const PipeHook* hook,
+                       const fora_balance* bal) {
   // a pipelined part always signals the next part, also when it stops early
   struct SignalOnExit {
     PipeLink* link;
@@ -318,6 +331,13 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
     if (rp.walk_scale != g->idx_scale || rp.alpha != g->idx_alpha)
       return fail(FORA_ERR_BAD_ARG, "the walk index was built for other alpha / eps / delta / p_f");
   }
+  if (!bal && dbg) bal = dbg->balance;
+  if (bal) {
+    if (!(bal->edge_push >= 0.0) || !(bal->push >= 0.0) || !(bal->walk >= 0.0) ||
+        !std::isfinite(bal->edge_push) || !std::isfinite(bal->push) || !std::isfinite(bal->walk))
+      return fail(FORA_ERR_BAD_ARG, "balance costs must be finite and >= 0");
+    if (indexed) return fail(FORA_ERR_BAD_ARG, "FORA_USE_INDEX cannot serve the balanced push");
+  }
   const bool given = (dbg_flags & FORA_DBG_GIVEN_PUSH) != 0;
   if (given && (!dbg || !dbg->reserve || !dbg->residue))
     return fail(FORA_ERR_BAD_ARG, "FORA_DBG_GIVEN_PUSH needs reserve and residue arrays");
@@ -331,7 +351,7 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
   const size_t N = (size_t)nsrc * (size_t)g->n;
   for (int i = 0; i < nsrc; ++i) {
     w->h_sources[i] = sources[i];
-    w->h_rmax[i] = rsrc.host ? rsrc.host[i] : rp.rmax;
+    w->h_rmax[i] = bal ? 1.0 : rsrc.host ? rsrc.host[i] : rp.rmax;
     if (!(w->h_rmax[i] > 0.0) || !std::isfinite(w->h_rmax[i]))
       return fail(FORA_ERR_BAD_ARG, "r_max of source %d must be positive and finite", i);
     if (indexed && !rsrc.device && w->h_rmax[i] > g->idx_rmax)
@@ -375,6 +395,15 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
   b.blk_cnt = w->blk;
   b.blk_walks = w->blk + w->residual_grid;
   b.residual_grid = w->residual_grid;
+  b.theta = w->rmax;
+  b.stopped = w->stopped;
+  if (bal) {
+    b.balance = 1;
+    b.bal_scale = b.zero_hop ? (1.0 - rp.alpha) * rp.walk_scale : rp.walk_scale;
+    b.cost_edge = bal->edge_push;
+    b.cost_push = bal->push;
+    b.cost_walk = bal->walk;
+  }
   bool host_loop;
   {
     std::lock_guard<std::mutex> tlock(g->mu);
@@ -455,7 +484,7 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
   if (async) return FORA_OK;
   CUDA_TRY(cudaMemcpyAsync(w->h_err, w->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
   if (st) CUDA_TRY(cudaMemcpyAsync(w->h_stats, w->stats, nsrc * sizeof(SlotStats), cudaMemcpyDeviceToHost, stream));
-  if (st && rsrc.device)
+  if (st && (rsrc.device || bal))  // the thresholds used were set on the device
     CUDA_TRY(cudaMemcpyAsync(w->h_rmax, w->rmax, nsrc * sizeof(double), cudaMemcpyDeviceToHost, stream));
   CUDA_TRY(cudaStreamSynchronize(stream));
   if (*w->h_err & kErrPushNotConverged)
@@ -498,7 +527,7 @@ constexpr int kMinPartSources = 32;
 
 int run_batch_pipelined(fora_graph* g, const fora_params* p, const int32_t* sources, int nsrc,
                         int32_t* out_ids, double* out_vals, fora_stats* st, cudaStream_t stream,
-                        RmaxSource rsrc, int parts) {
+                        RmaxSource rsrc, int parts, const fora_balance* bal) {
   CUDA_TRY(cudaSetDevice(g->device));
   {
     std::lock_guard<std::mutex> lock(g->mu);
@@ -538,7 +567,8 @@ int run_batch_pipelined(fora_graph* g, const fora_params* p, const int32_t* sour
           rcs[k] = run_batch_ws(g, &g->pipe_ws[k], p, sources + lo, hi - lo,
                                 out_ids ? out_ids + (size_t)lo * k_out : nullptr,
                                 out_vals ? out_vals + (size_t)lo * k_out : nullptr,
-                                st ? st + lo : nullptr, nullptr, 0, g->pipe_stream[k], rs, &hook);
+                                st ? st + lo : nullptr, nullptr, 0, g->pipe_stream[k], rs, &hook,
+                                bal);
           if (rcs[k]) errs[k] = g_err;
         });
       } catch (...) {  // no thread for part k: release every waiter, run no further part
@@ -567,7 +597,8 @@ int run_batch_pipelined(fora_graph* g, const fora_params* p, const int32_t* sour
 
 int run_batch(fora_graph* g, const fora_params* p, const int32_t* sources, int nsrc,
               int32_t* out_ids, double* out_vals, fora_stats* st, const fora_debug_io* dbg,
-              uint32_t dbg_flags, cudaStream_t stream, RmaxSource rsrc = RmaxSource()) {
+              uint32_t dbg_flags, cudaStream_t stream, RmaxSource rsrc = RmaxSource(),
+              const fora_balance* bal = nullptr) {
   int parts;
   {
     std::lock_guard<std::mutex> lock(g->mu);
@@ -575,9 +606,10 @@ int run_batch(fora_graph* g, const fora_params* p, const int32_t* sources, int n
   }
   parts = std::min(parts, nsrc / kMinPartSources);
   if (!dbg && parts > 1)
-    return run_batch_pipelined(g, p, sources, nsrc, out_ids, out_vals, st, stream, rsrc, parts);
+    return run_batch_pipelined(g, p, sources, nsrc, out_ids, out_vals, st, stream, rsrc, parts,
+                               bal);
   return run_batch_ws(g, &g->ws, p, sources, nsrc, out_ids, out_vals, st, dbg, dbg_flags, stream,
-                      rsrc);
+                      rsrc, nullptr, bal);
 }
 
 }  // namespace
@@ -853,6 +885,14 @@ int fora_ssppr_batch_rmax(fora_graph* g, const fora_params* params, const int32_
   rs.host = rmax;
   return run_batch(g, params, sources, nsrc, out_ids, out_vals, stats, nullptr, 0,
                    (cudaStream_t)stream, rs);
+}
+
+int fora_ssppr_batch_balanced(fora_graph* g, const fora_params* params, const fora_balance* costs,
+                              const int32_t* sources, int32_t nsrc, int32_t* out_ids,
+                              double* out_vals, fora_stats* stats, void* stream) {
+  if (!costs) return fail(FORA_ERR_BAD_ARG, "null balance costs");
+  return run_batch(g, params, sources, nsrc, out_ids, out_vals, stats, nullptr, 0,
+                   (cudaStream_t)stream, RmaxSource(), costs);
 }
 
 int fora_ssppr_batch_debug(fora_graph* g, const fora_params* params, const int32_t* sources,

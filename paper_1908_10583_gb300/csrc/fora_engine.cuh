@@ -74,6 +74,7 @@ struct SlotStats {
   unsigned long long walks;
   unsigned long long walk_steps;
   double rsum;
+  double moved;    // sum of alpha r(v) over the pushes (balanced push: r_sum = 1 - moved)
   uint32_t rounds;
   uint32_t pad;
 };
@@ -132,6 +133,14 @@ struct BatchDev {
   int spread_width;  // interleaved segments of the frontier the spread visits at once
   int walk_blocks;   // resident walk blocks per SM (3, 4 or 5)
   uint32_t max_rounds;  // push rounds allowed before kErrPushNotConverged
+  // Balanced push (Section 4.2, Alg. 3): balance != 0 makes rmax the per-source threshold
+  // theta (halved on the device when no node is above it) and stops a source's push before
+  // a round once cost_edge * edge pushes + cost_push * pushes >= ((1 - moved) * bal_scale)
+  // * cost_walk, with bal_scale = C' (C, or (1 - alpha) C with zero-hop pruning).
+  int balance;
+  double bal_scale, cost_edge, cost_push, cost_walk;
+  double* theta;       // [nsrc] the thresholds (the same array as rmax)
+  uint32_t* stopped;   // [nsrc] 1 once the cost rule stopped the source's push
 };
 
 // Launch-shape parameters of a graph (set through fora_graph_tune or the autotuner).

@@ -127,8 +127,21 @@ __global__ void k_push_seed(GraphDev g, BatchDev b) {
        slot += gridDim.x * blockDim.x) {
     // Alg. 1 starts from r(s) = 1.  The first pass of the loop body has an empty
     // frontier (nothing to spread); its take scans every source and finds F_0.
-    b.r[(unsigned long long)slot * (unsigned long long)g.n + (uint32_t)b.sources[slot]] = 1.0;
+    const uint32_t src = (uint32_t)b.sources[slot];
+    b.r[(unsigned long long)slot * (unsigned long long)g.n + src] = 1.0;
     b.alist[slot] = (uint32_t)slot;
+    if (b.balance) {
+      // the cost rule before any push: FC = 0 against the walk cost of r_sum = 1
+      const bool stop = 0.0 >= __dmul_rn(__dmul_rn(1.0, b.bal_scale), b.cost_walk);
+      b.stopped[slot] = stop ? 1u : 0u;
+      // Alg. 3 starts from threshold 1 and halves it while no node is above it: before the
+      // first push only r(s) = 1 is non-zero, so theta halves until 1 > theta d(s)
+      double theta = 1.0;
+      const double ds = (double)(g.row[src + 1] - g.row[src]);
+      if (!stop)
+        while (!(1.0 > __dmul_rn(theta, ds))) theta = __dmul_rn(0.5, theta);
+      b.theta[slot] = theta;
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     PushState* ps = b.ps;
@@ -290,7 +303,6 @@ __global__ void __launch_bounds__(kSpreadThreads, 6) k_push_spread(GraphDev g, B
 __global__ void __launch_bounds__(kTakeThreads, 3) k_push_take(GraphDev g, BatchDev b) {
   const PushState* ps = b.ps;
   const int nx = ps->cur ^ 1;
-  const uint32_t round = ps->round + 1;  // the take done here belongs to the next round
   const unsigned long long n = (unsigned long long)g.n;
   const unsigned long long tps = (n + kTileNodes - 1) / kTileNodes;
   const unsigned long long ntiles = (unsigned long long)ps->nact * tps;
@@ -310,6 +322,7 @@ __global__ void __launch_bounds__(kTakeThreads, 3) k_push_take(GraphDev g, Batch
   double* st_a = stage_a[threadIdx.x >> 5];
   for (unsigned long long t = blockIdx.x * wpb + (threadIdx.x >> 5); t < ntiles; t += nwarps) {
     const uint32_t s = b.alist[t / tps];
+    if (b.balance && b.stopped[s]) continue;  // warp-uniform: stopped before its first push
     const uint32_t tb = (uint32_t)((t % tps) * kTileNodes);
     const double rm = b.rmax[s];
     const float rmf = __double2float_rn(rm);
@@ -317,6 +330,7 @@ __global__ void __launch_bounds__(kTakeThreads, 3) k_push_take(GraphDev g, Batch
     const unsigned long long g0 = (unsigned long long)s * n;
     uint32_t t_cnt = 0;
     unsigned long long t_d = 0;
+    double t_moved = 0.0;  // this lane's alpha a of the tile (balanced push only)
 #pragma unroll 1
     for (uint32_t k0 = 0; k0 < kTileNodes / 32; k0 += 8) {
       // 256 consecutive nodes: residues and row offsets (nodes past n read row[n], so
@@ -408,7 +422,9 @@ __global__ void __launch_bounds__(kTakeThreads, 3) k_push_take(GraphDev g, Batch
           const unsigned long long gi = g0 + u;
           // the take of round `round`: reserve += alpha a, r = 0, spread increment
           b.r[gi] = 0.0;
-          b.res[gi] = __dadd_rn(rs, __dmul_rn(alpha, a));
+          const double moved = __dmul_rn(alpha, a);
+          b.res[gi] = __dadd_rn(rs, moved);
+          if (b.balance) t_moved = __dadd_rn(t_moved, moved);
           const unsigned long long qi = g0 + qb + e;
           qn[qi] = ((unsigned long long)s << 32) | u;
           b.fa[qi] = __dmul_rn(__dmul_rn(beta, a), inv);  // (1 - alpha) a / d
@@ -420,10 +436,14 @@ __global__ void __launch_bounds__(kTakeThreads, 3) k_push_take(GraphDev g, Batch
       }
       __syncwarp();
     }
+    if (b.balance && t_cnt) {  // warp-uniform
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t_moved = __dadd_rn(t_moved, __shfl_down_sync(kFull, t_moved, o));
+    }
     if (lane == 0 && t_cnt) {
       atomicAdd(&b.stats[s].pushes, (unsigned long long)t_cnt);
       atomicAdd(&b.stats[s].edge_pushes, t_d);
-      atomicMax(&b.stats[s].rounds, round);
+      if (b.balance) atomicAdd(&b.stats[s].moved, t_moved);
     }
   }
 }
@@ -448,13 +468,34 @@ __global__ void __launch_bounds__(1024) k_push_advance(BatchDev b,
     const int s = base + (int)threadIdx.x;
     const uint32_t c = s < nsrc ? cnt_nx[s] : 0u;
     const uint32_t h = s < nsrc ? hcnt_nx[s] : 0u;
+    // does the source's next take run: it found a frontier, or (balanced push) the cost
+    // rule lets it go on, with the threshold halved when no node was above it
+    bool take = c > 0;
+    if (s < nsrc && b.balance) {
+      if (b.stopped[s]) {
+        take = false;
+      } else {
+        const SlotStats& st = b.stats[s];
+        const double fc = __dadd_rn(__dmul_rn(b.cost_edge, (double)st.edge_pushes),
+                                    __dmul_rn(b.cost_push, (double)st.pushes));
+        const double wc = __dmul_rn(__dmul_rn(__dadd_rn(1.0, -st.moved), b.bal_scale), b.cost_walk);
+        if (fc >= wc) {
+          b.stopped[s] = 1u;  // the frontier just taken is still spread
+          take = false;
+        } else {
+          if (c == 0) b.theta[s] = __dmul_rn(0.5, b.theta[s]);
+          take = true;
+        }
+      }
+    }
+    if (s < nsrc && c > 0) b.stats[s].rounds += 1u;  // a push round of this source
     unsigned long long ge, he, gt, ht, ae, ze, at, zt;
     block_scan2((c + 31u) / 32u, h, &ge, &he, &gt, &ht);
-    block_scan2(c > 0 ? 1u : 0u, 0u, &ae, &ze, &at, &zt);
+    block_scan2(take ? 1u : 0u, 0u, &ae, &ze, &at, &zt);
     if (s < nsrc) {
       b.gpre[s] = carry_g + ge;
       b.hpre[s] = carry_h + he;
-      if (c > 0) b.alist[carry_a + ae] = (uint32_t)s;
+      if (take) b.alist[carry_a + ae] = (uint32_t)s;
       cnt_cur[s] = 0;  // counters of the frontier just spread: they serve the round after
       hcnt_cur[s] = 0;
     }
@@ -473,8 +514,10 @@ __global__ void __launch_bounds__(1024) k_push_advance(BatchDev b,
     b.work[0] = 0;  // dynamic work counters of the next spread
     b.work[16] = 0;
     // ps->round passes have run; the last one took the frontier of push round ps->round
-    // (the first pass only finds F_0), so going on is allowed while that is <= the cap
-    const bool more = carry_a > 0;
+    // (the first pass only finds F_0), so going on is allowed while that is <= the cap.
+    // Another pass is needed while a source takes again or a taken frontier waits for its
+    // spread (a source the cost rule just stopped).
+    const bool more = carry_a > 0 || carry_g > 0 || carry_h > 0;
     const bool go = more && ps->round <= b.max_rounds;
     if (more && !go) atomicOr(b.err, kErrPushNotConverged);
     ps->go = go ? 1u : 0u;

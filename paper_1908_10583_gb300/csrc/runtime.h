@@ -21,7 +21,8 @@ constexpr int kMaxResidualGrid = 4096;
 struct WorkspaceSizes {
   size_t N = 0;  // nsrc * n
   size_t r = 0, res = 0, tally = 0, q = 0, fa = 0, hub = 0, small = 0, work = 0, alist = 0,
-         slot_cnt = 0, pre = 0, ps = 0, err = 0, sources = 0, rmax = 0, stats = 0, blk = 0,
+         slot_cnt = 0, pre = 0, ps = 0, err = 0, sources = 0, rmax = 0, stats = 0, stopped = 0,
+         blk = 0,
          topk = 0, feat = 0, pred = 0, rmax_learned = 0, out_ids = 0, out_vals = 0;
   size_t total() const;  // q and hub count twice (two parities)
 };
@@ -40,9 +41,13 @@ struct PushGraphKey {
   double alpha = 0.0;
   int spread_width = 0;
   uint32_t max_rounds = 0;
+  int balance = 0;
+  double bal[4] = {0, 0, 0, 0};  // C', cost_edge, cost_push, cost_walk (balanced push)
   bool operator==(const PushGraphKey& o) const {
     return generation == o.generation && nsrc == o.nsrc && alpha == o.alpha &&
-           spread_width == o.spread_width && max_rounds == o.max_rounds;
+           spread_width == o.spread_width && max_rounds == o.max_rounds &&
+           balance == o.balance && bal[0] == o.bal[0] && bal[1] == o.bal[1] &&
+           bal[2] == o.bal[2] && bal[3] == o.bal[3];
   }
 };
 
@@ -67,6 +72,7 @@ struct Workspace {
   int32_t* sources = nullptr;
   double* rmax = nullptr;
   SlotStats* stats = nullptr;
+  uint32_t* stopped = nullptr;        // [nsrc] balanced push: the cost rule stopped the source
   unsigned long long* blk = nullptr;  // [2][residual_grid]
   int residual_grid = 0;
   void* topk_scratch = nullptr;
@@ -97,7 +103,7 @@ struct Workspace {
     dfree(ps);
     dfree(r); dfree(res); dfree(tally);
     dfree(q[0]); dfree(q[1]); dfree(hub[0]); dfree(hub[1]); dfree(fa);
-    dfree(small); dfree(work); dfree(alist); dfree(slot_cnt); dfree(pre); dfree(err); dfree(sources); dfree(rmax); dfree(stats); dfree(blk);
+    dfree(small); dfree(work); dfree(alist); dfree(slot_cnt); dfree(pre); dfree(err); dfree(sources); dfree(rmax); dfree(stats); dfree(stopped); dfree(blk);
     if (topk_scratch) cudaFree(topk_scratch);
     topk_scratch = nullptr;
     dfree(out_ids); dfree(out_vals); dfree(feat); dfree(pred); dfree(rmax_learned);
@@ -197,6 +203,7 @@ int reserve_workspace(fora_graph* g, Workspace* w, int nsrc);
 int run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p, const int32_t* sources,
                  int nsrc, int32_t* out_ids, double* out_vals, fora_stats* st,
                  const fora_debug_io* dbg, uint32_t dbg_flags, cudaStream_t stream,
-                 RmaxSource rsrc, const PipeHook* hook = nullptr);
+                 RmaxSource rsrc, const PipeHook* hook = nullptr,
+                 const fora_balance* bal = nullptr);
 
 }  // namespace fora

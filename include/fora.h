@@ -72,6 +72,7 @@ extern "C" {
 #define FORA_ERR_WALK_CAP (-6)           /* a walk exceeded FORA_MAX_WALK_STEPS moves */
 #define FORA_ERR_CUDA (-7)               /* a CUDA runtime call failed */
 #define FORA_ERR_TIMEOUT (-8)            /* a bounded wait ran out (serving) */
+#define FORA_ERR_BOUNDS (-9)             /* a device index check failed (FORA_DEBUG builds) */
 
 #define FORA_MAX_PUSH_ROUNDS 100000
 #define FORA_MAX_WALK_STEPS 16384
@@ -296,8 +297,11 @@ int fora_ssppr_batch_learned(fora_graph *g, const fora_params *params, fora_mode
  * max_batch.  Requests queue per graph; a free lane admits the oldest queued requests
  * that share everything but k (up to its slots; after waiting up to batch_window_ms for
  * more when fewer are queued), runs them as one batched query with the largest k, and
- * returns each request its own top-k.  Lanes run concurrently, so requests that arrive
- * while others are on the GPU start as soon as a lane frees up and overlap with them.
+ * returns each request its own top-k.  With admit_during_push, requests that arrive while
+ * a batch is in its push rounds join it between two rounds, as long as it has free slots
+ * and they share its parameters (k at most the batch's k).  Lanes run concurrently, so
+ * requests that arrive while others are on the GPU also start as soon as a lane frees up
+ * and overlap with them.
  * A request's result equals the same query run alone (same Philox counters), up to the
  * FP64 rounding order of the push.
  */
@@ -306,12 +310,19 @@ typedef struct {
   int32_t lanes_per_graph;
   int32_t max_batch;
   double batch_window_ms;
+  int32_t admit_during_push; /* 1: a running batch takes compatible arrivals into its free
+                                slots between two push rounds (its rounds then run from a
+                                host loop); 0: arrivals wait for a free lane */
+  int32_t pad;
 } fora_server_config;
 
 typedef struct {
   double submit_ms, start_ms, end_ms; /* since the server was created */
   uint32_t batch_size;                /* queries in the batch that served the request */
   int32_t lane;
+  uint32_t joined;                    /* 1: admitted into a running batch between two of its
+                                         push rounds (admit_during_push) */
+  uint32_t pad;
   fora_stats stats;
 } fora_request_info;
 
@@ -331,9 +342,10 @@ int fora_server_submit(fora_server *s, int32_t graph, int32_t source, const fora
  * ticket.  Any output may be NULL. */
 int fora_server_wait(fora_server *s, uint64_t ticket, double timeout_ms, int32_t *out_ids,
                      double *out_vals, fora_request_info *info);
-/* Requests completed, batches run, and the most lanes that were busy at once. */
+/* Requests completed, batches run, the most lanes that were busy at once, and requests
+ * that joined a batch during its push rounds.  Any output may be NULL. */
 int fora_server_stats(fora_server *s, uint64_t *completed, uint64_t *batches,
-                      int32_t *max_concurrent);
+                      int32_t *max_concurrent, uint64_t *joined);
 
 /* ---- inspection entry points (parity testing) ---- */
 
@@ -487,6 +499,15 @@ int fora_workspace_bytes(int64_t n, const int64_t *row_ptr, int32_t nsrc, uint64
  * injection off.  The paper has no counterpart.  FORA_ERR_BAD_ARG for nth < 0.
  */
 int fora_debug_fail_alloc(int64_t nth);
+
+/*
+ * 1 if this library was built with FORA_DEBUG: the hot kernels then check their device
+ * indexes (nodes, edges, queue and hub-item slots, residual entries, walk-end tallies)
+ * against the buffer sizes, skip an access that would fall outside and report it as
+ * FORA_ERR_BOUNDS instead of touching memory; 0 for the normal build.  The paper has no
+ * counterpart.
+ */
+int fora_debug_checks(void);
 
 /* Message of the calling thread's last failure ("" if none): the error channel of the
  * conventions above (no exception crosses the ABI); the string stays valid until the

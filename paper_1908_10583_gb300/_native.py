@@ -24,6 +24,7 @@ FORA_ERR_PUSH_NOT_CONVERGED = -5
 FORA_ERR_WALK_CAP = -6
 FORA_ERR_CUDA = -7
 FORA_ERR_TIMEOUT = -8
+FORA_ERR_BOUNDS = -9
 FORA_MAX_K = 4096
 FORA_OUT_DEVICE = 0x1
 FORA_ASYNC = 0x2
@@ -70,13 +71,15 @@ class Stats(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("memory_budget_bytes", ctypes.c_uint64), ("lanes_per_graph", ctypes.c_int32),
-                ("max_batch", ctypes.c_int32), ("batch_window_ms", ctypes.c_double)]
+                ("max_batch", ctypes.c_int32), ("batch_window_ms", ctypes.c_double),
+                ("admit_during_push", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class RequestInfo(ctypes.Structure):
     _fields_ = [("submit_ms", ctypes.c_double), ("start_ms", ctypes.c_double),
                 ("end_ms", ctypes.c_double), ("batch_size", ctypes.c_uint32),
-                ("lane", ctypes.c_int32), ("stats", Stats)]
+                ("lane", ctypes.c_int32), ("joined", ctypes.c_uint32), ("pad", ctypes.c_uint32),
+                ("stats", Stats)]
 
 
 class Balance(ctypes.Structure):
@@ -92,7 +95,8 @@ class DebugIO(ctypes.Structure):
 
 
 def lib_path() -> str:
-    return _build.LIB_PATH
+    """The library this process loads: the FORA_DEBUG build when FORA_LIB_DEBUG=1."""
+    return _build.DEBUG_LIB_PATH if os.environ.get("FORA_LIB_DEBUG") == "1" else _build.LIB_PATH
 
 
 def load():
@@ -101,10 +105,11 @@ def load():
     with _lock:
         if _lib is not None:
             return _lib
-        if not os.path.exists(_build.LIB_PATH):
-            raise RuntimeError(f"{_build.LIB_PATH} is missing: the CUDA library must be built "
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: the CUDA library must be built "
                                "(paper_1908_10583_gb300.build.build()); there is no CPU fallback")
-        L = ctypes.CDLL(_build.LIB_PATH)
+        L = ctypes.CDLL(path)
         P, I, i64, i32, u32 = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int32,
                                ctypes.c_uint32)
         L.fora_graph_create.restype = I
@@ -166,7 +171,7 @@ def load():
         L.fora_server_wait.restype = I
         L.fora_server_wait.argtypes = [P, ctypes.c_uint64, ctypes.c_double, P, P, P]
         L.fora_server_stats.restype = I
-        L.fora_server_stats.argtypes = [P, P, P, P]
+        L.fora_server_stats.argtypes = [P, P, P, P, P]
         L.fora_graph_autotune.restype = I
         L.fora_graph_autotune.argtypes = [P, ctypes.POINTER(Params), P, i32, P, P, P]
         L.fora_graph_tune.restype = I
@@ -183,6 +188,8 @@ def load():
         L.fora_index_destroy.argtypes = [P]
         L.fora_workspace_bytes.restype = I
         L.fora_workspace_bytes.argtypes = [i64, P, i32, P]
+        L.fora_debug_checks.restype = I
+        L.fora_debug_checks.argtypes = []
         L.fora_debug_fail_alloc.restype = I
         L.fora_debug_fail_alloc.argtypes = [i64]
         L.fora_last_error.restype = ctypes.c_char_p
@@ -569,11 +576,11 @@ class Server:
     """Continuous-batching request loop over resident graphs (fora_server_*)."""
 
     def __init__(self, graphs, lanes_per_graph=2, max_batch=256, memory_budget_bytes=0,
-                 batch_window_ms=0.5):
+                 batch_window_ms=0.5, admit_during_push=True):
         self._graphs = list(graphs)  # keep the graphs alive
         arr = (ctypes.c_void_p * len(self._graphs))(*[g._h.value for g in self._graphs])
         cfg = ServerConfig(int(memory_budget_bytes), int(lanes_per_graph), int(max_batch),
-                           float(batch_window_ms))
+                           float(batch_window_ms), 1 if admit_during_push else 0, 0)
         h = ctypes.c_void_p()
         _check(load().fora_server_create(ctypes.cast(arr, ctypes.c_void_p), len(self._graphs),
                                          ctypes.byref(cfg), ctypes.byref(h)))
@@ -611,6 +618,8 @@ class Server:
         return ids, vals, info
 
     def stats(self):
-        c, b, m = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int32()
-        _check(load().fora_server_stats(self._h, ctypes.byref(c), ctypes.byref(b), ctypes.byref(m)))
-        return {"completed": c.value, "batches": b.value, "max_concurrent_lanes": m.value}
+        c, b, m, j = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int32(), ctypes.c_uint64()
+        _check(load().fora_server_stats(self._h, ctypes.byref(c), ctypes.byref(b), ctypes.byref(m),
+                                        ctypes.byref(j)))
+        return {"completed": c.value, "batches": b.value, "max_concurrent_lanes": m.value,
+                "joined": j.value}

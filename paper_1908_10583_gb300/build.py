@@ -3,7 +3,9 @@
 The translation units compile in parallel and link into
 ``paper_1908_10583_gb300/_build/libfora.so`` (static CUDA runtime).  Set
 ``FORA_PTXAS_VERBOSE=1`` to print the register and shared-memory use of every
-kernel.
+kernel.  ``build(debug=True)`` builds ``_build/debug/libfora_debug.so`` with
+``-DFORA_DEBUG`` (device index checks that report FORA_ERR_BOUNDS); the package
+loads it instead of the normal library when ``FORA_LIB_DEBUG=1`` is set.
 """
 from __future__ import annotations
 
@@ -17,6 +19,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libfora.so")
+DEBUG_DIR = os.path.join(BUILD_DIR, "debug")
+DEBUG_LIB_PATH = os.path.join(DEBUG_DIR, "libfora_debug.so")
 SOURCES = ["push.cu", "walk.cu", "topk.cu", "capi.cu", "topk_noalloc.cu", "learn.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -43,23 +47,26 @@ def _deps():
     return files
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB_PATH):
+def up_to_date(lib: str = LIB_PATH) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB_PATH)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every CUDA translation unit and link libfora.so; returns its path."""
-    if not force and up_to_date():
-        return LIB_PATH
-    os.makedirs(BUILD_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Compile every CUDA translation unit and link libfora.so (or, with debug, the
+    FORA_DEBUG library); returns its path."""
+    lib = DEBUG_LIB_PATH if debug else LIB_PATH
+    out_dir = DEBUG_DIR if debug else BUILD_DIR
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
-    flags = _flags()
+    flags = _flags() + (["-DFORA_DEBUG"] if debug else [])
 
     def compile_one(src):
-        obj = os.path.join(BUILD_DIR, os.path.splitext(src)[0] + ".o")
+        obj = os.path.join(out_dir, os.path.splitext(src)[0] + ".o")
         cmd = [nvcc, "-c", os.path.join(CSRC, src), "-o", obj, *flags]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
@@ -70,13 +77,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc, "-shared", *ARCH, "-o", tmp, *objs, "-lpthread"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stderr}")
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -304,7 +304,7 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
                        const int32_t* sources, int nsrc, int32_t* out_ids, double* out_vals,
                        fora_stats* st, const fora_debug_io* dbg, uint32_t dbg_flags,
                        cudaStream_t stream, RmaxSource rsrc, const PipeHook* hook,
-                       const fora_balance* bal) {
+                       const fora_balance* bal, const JoinHook* join) {
   // a pipelined part always signals the next part, also when it stops early
   struct SignalOnExit {
     PipeLink* link;
@@ -332,6 +332,8 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
       return fail(FORA_ERR_BAD_ARG, "the walk index was built for other alpha / eps / delta / p_f");
   }
   if (!bal && dbg) bal = dbg->balance;
+  if (join && (join->cap < nsrc || join->cap > 65535 || bal || dbg || !join->poll))
+    return fail(FORA_ERR_BAD_ARG, "a joining batch needs cap >= nsrc and no balance or debug");
   if (bal) {
     if (!(bal->edge_push >= 0.0) || !(bal->push >= 0.0) || !(bal->walk >= 0.0) ||
         !std::isfinite(bal->edge_push) || !std::isfinite(bal->push) || !std::isfinite(bal->walk))
@@ -346,9 +348,9 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
 
   std::lock_guard<std::mutex> lock(w->mu);
   CUDA_TRY(cudaSetDevice(g->device));
-  rc = ensure_workspace(g, w, nsrc);
+  rc = ensure_workspace(g, w, join ? join->cap : nsrc);
   if (rc) return rc;
-  const size_t N = (size_t)nsrc * (size_t)g->n;
+  size_t N = (size_t)nsrc * (size_t)g->n;
   for (int i = 0; i < nsrc; ++i) {
     w->h_sources[i] = sources[i];
     w->h_rmax[i] = bal ? 1.0 : rsrc.host ? rsrc.host[i] : rp.rmax;
@@ -368,6 +370,7 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
   CUDA_TRY(cudaMemsetAsync(w->stats, 0, nsrc * sizeof(SlotStats), stream));
 
   const GraphDev gd = g->dev();
+  const size_t n64 = (size_t)g->n;
   BatchDev b{};
   b.nsrc = nsrc;
   b.alpha = rp.alpha;
@@ -382,8 +385,9 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
   b.hub[0] = w->hub[0]; b.hub[1] = w->hub[1];
   b.hub_stride = g->hub_chunks;
   b.slot_cnt = w->slot_cnt;
+  b.cnt_stride = w->cap;
   b.gpre = w->pre;
-  b.hpre = w->pre + (nsrc + 1);
+  b.hpre = w->pre + (w->cap + 1);
   b.alist = w->alist;
   b.work = w->work;
   b.ps = w->ps;
@@ -426,9 +430,39 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
     CUDA_TRY(cudaMemsetAsync(w->r, 0, N * sizeof(double), stream));
     CUDA_TRY(cudaMemsetAsync(w->res, 0, N * sizeof(double), stream));
     CUDA_TRY(cudaMemsetAsync(w->work, 0, 32 * sizeof(unsigned long long), stream));
-    CUDA_TRY(cudaMemsetAsync(w->slot_cnt, 0, 4 * (size_t)nsrc * sizeof(uint32_t), stream));
+    CUDA_TRY(cudaMemsetAsync(w->slot_cnt, 0, 4 * (size_t)w->cap * sizeof(uint32_t), stream));
     CUDA_TRY(launch_push_seed(gd, b, stream));
-    if (host_loop) {
+    if (join) {
+      // rounds from a host loop; after each round further sources may join as new slots
+      uint32_t go = 1;
+      while (go) {
+        CUDA_TRY(launch_push_body(gd, b, g->num_sms, 0, false, stream));
+        CUDA_TRY(cudaMemcpyAsync(w->go_host, &w->ps->go, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                 stream));
+        CUDA_TRY(cudaStreamSynchronize(stream));
+        go = *w->go_host;
+        const int room = join->cap - b.nsrc;
+        const int k = room > 0 ? join->poll(w->h_sources + b.nsrc, room) : 0;
+        if (k <= 0) continue;
+        const int first = b.nsrc;
+        for (int i = first; i < first + k; ++i) w->h_rmax[i] = rp.rmax;
+        CUDA_TRY(cudaMemcpyAsync(w->sources + first, w->h_sources + first, k * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, stream));
+        CUDA_TRY(cudaMemcpyAsync(w->rmax + first, w->h_rmax + first, k * sizeof(double),
+                                 cudaMemcpyHostToDevice, stream));
+        const size_t off = (size_t)first * n64, len = (size_t)k * n64;
+        CUDA_TRY(cudaMemsetAsync(w->r + off, 0, len * sizeof(double), stream));
+        CUDA_TRY(cudaMemsetAsync(w->res + off, 0, len * sizeof(double), stream));
+        CUDA_TRY(cudaMemsetAsync(w->tally + off, 0, len * sizeof(Tally), stream));
+        CUDA_TRY(cudaMemsetAsync(w->stats + first, 0, k * sizeof(SlotStats), stream));
+        b.nsrc = first + k;
+        CUDA_TRY(launch_push_join(gd, b, first, k, stream));
+        go = 1;
+      }
+      nsrc = b.nsrc;
+      N = (size_t)nsrc * n64;
+      if (join->nsrc_final) *join->nsrc_final = nsrc;
+    } else if (host_loop) {
       // the same round kernels launched one round at a time from the host (for profilers
       // that cannot look inside conditional graph nodes); one host round trip per round
       uint32_t go = 1;
@@ -491,6 +525,8 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
     return fail(FORA_ERR_PUSH_NOT_CONVERGED, "push did not converge in %u rounds", b.max_rounds);
   if (*w->h_err & kErrWalkOverflow) return fail(FORA_ERR_WALK_OVERFLOW, "a source needs 2^32 or more walks");
   if (*w->h_err & kErrWalkCap) return fail(FORA_ERR_WALK_CAP, "a walk exceeded %d moves", FORA_MAX_WALK_STEPS);
+  if (*w->h_err & kErrBounds)
+    return fail(FORA_ERR_BOUNDS, "a device index check failed (this is a FORA_DEBUG build)");
   if (*w->h_err & kErrIndexRange)
     return fail(FORA_ERR_BAD_ARG, "a residue needs more walks than the walk index holds (r_max above the index's)");
   if (st) {
@@ -507,7 +543,7 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
       o.walks = s.walks;
       o.walk_steps = s.walk_steps;
       o.push_rounds = s.rounds;
-      o.source = sources[i];
+      o.source = w->h_sources[i];
       o.ms_push = ms[0];
       o.ms_residual = ms[1];
       o.ms_walk = ms[2];
@@ -761,8 +797,9 @@ int fora_index_build(fora_graph* g, const fora_params* params, void* stream_) {
   b.hub[0] = w->hub[0]; b.hub[1] = w->hub[1];
   b.hub_stride = g->hub_chunks;
   b.slot_cnt = w->slot_cnt;
+  b.cnt_stride = w->cap;
   b.gpre = w->pre;
-  b.hpre = w->pre + 2;
+  b.hpre = w->pre + (w->cap + 1);
   b.alist = w->alist;
   b.work = w->work;
   b.ps = w->ps;
@@ -1410,6 +1447,14 @@ int fora_workspace_bytes(int64_t n, const int64_t* row_ptr, int32_t nsrc, uint64
   }
   *bytes = (uint64_t)workspace_sizes(n, hub_chunks, nsrc).total();
   return FORA_OK;
+}
+
+int fora_debug_checks(void) {
+#ifdef FORA_DEBUG
+  return 1;
+#else
+  return 0;
+#endif
 }
 
 int fora_debug_fail_alloc(int64_t nth) {

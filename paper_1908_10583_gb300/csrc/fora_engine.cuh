@@ -23,6 +23,24 @@ constexpr uint32_t kErrWalkCap = 1u;
 constexpr uint32_t kErrWalkOverflow = 2u;
 constexpr uint32_t kErrPushNotConverged = 4u;
 constexpr uint32_t kErrIndexRange = 8u;  // a residue needs more walks than the index holds
+constexpr uint32_t kErrBounds = 16u;     // a device index check failed (FORA_DEBUG builds)
+
+// Device index checks of the FORA_DEBUG build: FORA_IN_RANGE(err, i, n) is true when
+// i < n; otherwise it records kErrBounds in *err and is false, and the caller skips the
+// access (the query then fails with FORA_ERR_BOUNDS).  In other builds it is `true` and
+// costs nothing.
+#ifdef FORA_DEBUG
+__device__ __forceinline__ bool in_range_checked(uint32_t* err, unsigned long long i,
+                                                 unsigned long long n) {
+  if (i < n) return true;
+  atomicOr(err, kErrBounds);
+  return false;
+}
+#define FORA_IN_RANGE(err, i, n) \
+  ::fora::in_range_checked((err), (unsigned long long)(i), (unsigned long long)(n))
+#else
+#define FORA_IN_RANGE(err, i, n) true
+#endif
 constexpr uint32_t kMaxPushRounds = 100000u;  // default cap of the push rounds
 
 // Where the push loop stands: the parity of the current frontier queue, the number of
@@ -112,7 +130,8 @@ struct BatchDev {
   double* fa;                // per frontier entry: (1 - alpha) r(v) / d(v)
   unsigned long long* hub[2];  // hub chunk items: (q index << kHubChunkBits) | chunk
   unsigned long long hub_stride;
-  uint32_t* slot_cnt;        // [4][nsrc]: entries of parity 0, 1; hub items of parity 0, 1
+  uint32_t* slot_cnt;        // [4][cnt_stride]: entries of parity 0, 1; hub items of parity 0, 1
+  int cnt_stride;            // slots per row of slot_cnt (the workspace's capacity)
   unsigned long long* gpre;  // [nsrc + 1]: exclusive prefix of ceil(entries / 32), current
   unsigned long long* hpre;  // [nsrc + 1]: exclusive prefix of hub items, current
   uint32_t* alist;           // [nsrc]: the sources with a non-empty current frontier
@@ -168,6 +187,9 @@ cudaError_t device_alloc(void** p, size_t bytes);
 cudaError_t launch_push_seed(const GraphDev& g, const BatchDev& b, cudaStream_t st);
 cudaError_t launch_push_body(const GraphDev& g, const BatchDev& b, int num_sms,
                              cudaGraphConditionalHandle loop, bool in_graph, cudaStream_t st);
+// push.cu: slots [first, first + k) join a batch between two push rounds (host loop only).
+cudaError_t launch_push_join(const GraphDev& g, const BatchDev& b, int first, int k,
+                             cudaStream_t st);
 // push.cu: the frontier test r > RN(r_max * d) of the take, on given triples.
 cudaError_t launch_threshold_table(const double* r, const double* rm, const uint32_t* d,
                                    uint8_t* out, int count, cudaStream_t st);

@@ -161,13 +161,14 @@ __global__ void k_push_seed(GraphDev g, BatchDev b) {
 // first lane (k copies counted with multiplicity, as Alg. 1 pushes along each of them;
 // one rounding instead of k, which only reorders the FP64 sum like the atomics do).
 __device__ __forceinline__ void spread_slice(double* r, unsigned long long base, uint32_t u,
-                                             uint32_t owner, double inc, bool act) {
+                                             uint32_t owner, double inc, bool act,
+                                             uint32_t* err, unsigned long long n) {
   const uint32_t lane = lane_id();
   const uint32_t pu = __shfl_up_sync(kFull, u, 1);
   const uint32_t po = __shfl_up_sync(kFull, owner, 1);
   const bool cont = act && lane > 0 && pu == u && po == owner;  // continues lane - 1's run
   const uint32_t brk = __ballot_sync(kFull, !cont);              // run starts and idle lanes
-  if (act && !cont) {
+  if (act && !cont && FORA_IN_RANGE(err, u, n)) {
     const uint32_t above = brk & ~((2u << lane) - 1u);
     const uint32_t k = (above ? (uint32_t)__ffs(above) - 1u : 32u) - lane;
     atomicAdd(&r[base + u], k == 1u ? inc : __dmul_rn(inc, (double)k));
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(kSpreadThreads, 6) k_push_spread(GraphDev g, B
   const unsigned long long ngroups = b.ps->ngroups;
   const unsigned long long nh = b.ps->nhub;
   const unsigned long long* q = b.q[cur];
-  const uint32_t* cnt = b.slot_cnt + (size_t)cur * b.nsrc;
+  const uint32_t* cnt = b.slot_cnt + (size_t)cur * b.cnt_stride;
   const uint32_t lane = lane_id();
   const unsigned long long n = (unsigned long long)g.n;
 
@@ -248,7 +249,8 @@ __global__ void __launch_bounds__(kSpreadThreads, 6) k_push_spread(GraphDev g, B
           u[k] = act[k] ? (uint32_t)g.col[rbk + (e - ek)] : 0u;
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) spread_slice(b.r, base_gi, u[k], own[k], ik[k], act[k]);
+        for (int k = 0; k < 4; ++k)
+          spread_slice(b.r, base_gi, u[k], own[k], ik[k], act[k], b.err, n);
       }
     }
   }
@@ -290,7 +292,7 @@ __global__ void __launch_bounds__(kSpreadThreads, 6) k_push_spread(GraphDev g, B
       }
 #pragma unroll
       for (int k = 0; k < (int)(kHubChunk / 32); ++k)
-        spread_slice(b.r, gbase, u[k], 0u, inc, u[k] != 0xFFFFFFFFu);
+        spread_slice(b.r, gbase, u[k], 0u, inc, u[k] != 0xFFFFFFFFu, b.err, n);
     }
   }
 }
@@ -306,8 +308,8 @@ __global__ void __launch_bounds__(kTakeThreads, 3) k_push_take(GraphDev g, Batch
   const unsigned long long n = (unsigned long long)g.n;
   const unsigned long long tps = (n + kTileNodes - 1) / kTileNodes;
   const unsigned long long ntiles = (unsigned long long)ps->nact * tps;
-  uint32_t* cnt_nx = b.slot_cnt + (size_t)nx * b.nsrc;
-  uint32_t* hcnt_nx = b.slot_cnt + (size_t)(2 + nx) * b.nsrc;
+  uint32_t* cnt_nx = b.slot_cnt + (size_t)nx * b.cnt_stride;
+  uint32_t* hcnt_nx = b.slot_cnt + (size_t)(2 + nx) * b.cnt_stride;
   unsigned long long* qn = b.q[nx];
   unsigned long long* hn = b.hub[nx];
   const double alpha = b.alpha, beta = __dadd_rn(1.0, -b.alpha);
@@ -418,9 +420,10 @@ __global__ void __launch_bounds__(kTakeThreads, 3) k_push_take(GraphDev g, Batch
         }
         const uint32_t nch = live ? hub_chunks_of(dk) : 0u;
         const uint32_t nch_incl = hsum ? warp_incl_scan(nch) : 0u;  // lower entries first
-        if (live) {
+        if (live && FORA_IN_RANGE(b.err, qb + e, n) &&
+            FORA_IN_RANGE(b.err, hp + nch_incl, b.hub_stride + 1)) {
           const unsigned long long gi = g0 + u;
-          // the take of round `round`: reserve += alpha a, r = 0, spread increment
+          // the take: reserve += alpha a, r = 0, spread increment
           b.r[gi] = 0.0;
           const double moved = __dmul_rn(alpha, a);
           b.res[gi] = __dadd_rn(rs, moved);
@@ -457,10 +460,11 @@ __global__ void __launch_bounds__(1024) k_push_advance(BatchDev b,
   PushState* ps = b.ps;
   const int cur = ps->cur, nx = cur ^ 1;
   const int nsrc = b.nsrc;
-  const uint32_t* cnt_nx = b.slot_cnt + (size_t)nx * nsrc;
-  const uint32_t* hcnt_nx = b.slot_cnt + (size_t)(2 + nx) * nsrc;
-  uint32_t* cnt_cur = b.slot_cnt + (size_t)cur * nsrc;
-  uint32_t* hcnt_cur = b.slot_cnt + (size_t)(2 + cur) * nsrc;
+  const size_t cs = (size_t)b.cnt_stride;
+  const uint32_t* cnt_nx = b.slot_cnt + (size_t)nx * cs;
+  const uint32_t* hcnt_nx = b.slot_cnt + (size_t)(2 + nx) * cs;
+  uint32_t* cnt_cur = b.slot_cnt + (size_t)cur * cs;
+  uint32_t* hcnt_cur = b.slot_cnt + (size_t)(2 + cur) * cs;
   __shared__ unsigned long long carry_g, carry_h, carry_a;
   if (threadIdx.x == 0) { carry_g = 0; carry_h = 0; carry_a = 0; }
   __syncthreads();
@@ -525,6 +529,26 @@ __global__ void __launch_bounds__(1024) k_push_advance(BatchDev b,
   }
 }
 
+// Sources joining a batch between two push rounds (serving): slots [first, first + k)
+// (their sources, r_max and zeroed state already in place) get r(s) = 1 and enter the next
+// take, and the frontier prefixes are extended over them (empty frontiers).  One block.
+// The push of a source depends only on its own residues, so a source that joins later runs
+// the same rounds as it would from the start.
+__global__ void k_push_join(GraphDev g, BatchDev b, int first, int k) {
+  PushState* ps = b.ps;
+  const unsigned long long gtot = b.gpre[first], htot = b.hpre[first];
+  const uint32_t nact = ps->nact;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    const int slot = first + i;
+    b.r[(unsigned long long)slot * (unsigned long long)g.n + (uint32_t)b.sources[slot]] = 1.0;
+    b.alist[nact + i] = (uint32_t)slot;
+    b.gpre[slot + 1] = gtot;
+    b.hpre[slot + 1] = htot;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) ps->nact = nact + (uint32_t)k;
+}
+
 // The frontier test of k_push_take on given (r, r_max, d) triples.
 __global__ void k_threshold_table(const double* r, const double* rm, const uint32_t* d,
                                   uint8_t* out, int count) {
@@ -541,6 +565,13 @@ cudaError_t launch_threshold_table(const double* r, const double* rm, const uint
                                    uint8_t* out, int count, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   k_threshold_table<<<(count + 255) / 256, 256, 0, st>>>(r, rm, d, out, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_push_join(const GraphDev& g, const BatchDev& b, int first, int k,
+                             cudaStream_t st) {
+  if (k <= 0) return cudaSuccess;
+  k_push_join<<<1, 256, 0, st>>>(g, b, first, k);
   return cudaGetLastError();
 }
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <condition_variable>
+#include <functional>
 #include <mutex>
 
 #include "fora.h"
@@ -160,6 +161,17 @@ struct PipeHook {
 };
 constexpr int kMaxPipeline = 4;
 
+// Admission of further sources while a batch is in its push rounds (the serving lanes):
+// the rounds run from a host loop, and after each round `poll` may write up to `room`
+// sources to `dst` (HOST) and returns how many; they join the batch as its next slots and
+// their queries run exactly as they would alone.  The batch then has *nsrc_final sources
+// (outputs and stats are sized for `cap`).
+struct JoinHook {
+  int cap = 0;
+  std::function<int(int32_t* dst, int room)> poll;
+  int* nsrc_final = nullptr;
+};
+
 }  // namespace fora
 
 struct fora_graph {
@@ -204,6 +216,6 @@ int run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p, const int32_
                  int nsrc, int32_t* out_ids, double* out_vals, fora_stats* st,
                  const fora_debug_io* dbg, uint32_t dbg_flags, cudaStream_t stream,
                  RmaxSource rsrc, const PipeHook* hook = nullptr,
-                 const fora_balance* bal = nullptr);
+                 const fora_balance* bal = nullptr, const JoinHook* join = nullptr);
 
 }  // namespace fora

@@ -1,13 +1,14 @@
 // Serving runtime: continuous batching of SSPPR queries over resident graphs.
 //
 // Each graph gets `lanes_per_graph` lanes.  A lane owns a workspace sized for its slot
-// capacity (the HBM budget divided over the lanes, at about 56 bytes per node per
-// query for the residue, reserve, walk tallies and frontiers), a CUDA stream and a host
+// capacity (the HBM budget divided over the lanes, by the workspace's own buffer sizes
+// per query slot: residue, reserve, walk tallies, frontiers), a CUDA stream and a host
 // thread.  Requests queue per graph; a free lane admits as many compatible queued
-// requests as it has slots (after a short batching window when fewer are waiting),
-// runs them as one batched query on its stream, and hands the results back.  While one
-// lane's batch is on the GPU the next arrivals are admitted by another lane, so batches
-// overlap on the device and slots refill as batches finish.
+// requests as it has slots (after a short batching window when fewer are waiting) and
+// runs them as one batched query on its stream.  While that batch is in its push rounds,
+// requests that arrive take the batch's free slots between two rounds (admit_during_push)
+// and share its walk phase; while one lane's batch is on the GPU the next arrivals are
+// also admitted by another lane, so batches overlap on the device.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -82,7 +83,7 @@ struct fora_server {
   std::vector<std::unique_ptr<Lane>> lanes;
   bool stop = false;
   Clock::time_point t0 = Clock::now();
-  uint64_t batches = 0, completed = 0, batched_queries = 0;
+  uint64_t batches = 0, completed = 0, batched_queries = 0, joined = 0;
   int lanes_busy = 0, max_lanes_busy = 0;
 
   double now_ms() const {
@@ -135,14 +136,42 @@ struct fora_server {
       fora_params p = first;
       p.k = kmax;
       p.flags &= ~(FORA_OUT_DEVICE | FORA_ASYNC);
-      const int nb = (int)batch.size();
-      ids.resize((size_t)nb * kmax);
-      vals.resize((size_t)nb * kmax);
-      st.resize(nb);
+      int nb = (int)batch.size();
+      ids.resize((size_t)L->cap * kmax);
+      vals.resize((size_t)L->cap * kmax);
+      st.resize(L->cap);
+      // continuous admission: between two push rounds, compatible requests that arrived
+      // meanwhile (k <= the batch's k) take free slots of this batch
+      JoinHook hook;
+      hook.cap = L->cap;
+      hook.nsrc_final = &nb;
+      hook.poll = [&](int32_t* dst, int room) {
+        std::lock_guard<std::mutex> g2(mu);
+        int added = 0;
+        const double t_join = now_ms();
+        for (auto it = q.begin(); it != q.end() && added < room;) {
+          Request& r = reqs[*it];
+          if (compatible(r.params, first) && r.params.k <= kmax) {
+            r.status = 1;
+            r.info.start_ms = t_join;
+            r.info.joined = 1;
+            dst[added++] = r.source;
+            batch.push_back(*it);
+            it = q.erase(it);
+          } else {
+            ++it;
+          }
+        }
+        joined += (uint64_t)added;
+        return added;
+      };
+      const bool admit = cfg.admit_during_push != 0;
       const int rc = run_batch_ws(g, &L->ws, &p, src.data(), nb, ids.data(), vals.data(), st.data(),
-                                  nullptr, 0, L->stream, RmaxSource());
+                                  nullptr, 0, L->stream, RmaxSource(), nullptr, nullptr,
+                                  admit ? &hook : nullptr);
       const std::string err = rc ? fora_last_error() : "";
       const double t_end = now_ms();
+      nb = (int)batch.size();
 
       lk.lock();
       --lanes_busy;
@@ -296,12 +325,14 @@ int fora_server_wait(fora_server* s, uint64_t ticket, double timeout_ms, int32_t
   return FORA_OK;
 }
 
-int fora_server_stats(fora_server* s, uint64_t* completed, uint64_t* batches, int32_t* max_concurrent) {
+int fora_server_stats(fora_server* s, uint64_t* completed, uint64_t* batches, int32_t* max_concurrent,
+                      uint64_t* joined) {
   if (!s) return report_error(FORA_ERR_BAD_ARG, "null server");
   std::lock_guard<std::mutex> lk(s->mu);
   if (completed) *completed = s->completed;
   if (batches) *batches = s->batches;
   if (max_concurrent) *max_concurrent = s->max_lanes_busy;
+  if (joined) *joined = s->joined;
   return FORA_OK;
 }
 

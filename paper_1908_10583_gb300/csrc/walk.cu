@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(kResidualThreads) k_residual_emit(GraphDev g, 
     const bool live = omega >= 1;
     unsigned long long ce, we, ct, wt;
     block_excl_scan2(live ? 1ull : 0ull, omega, &ce, &we, &ct, &wt);
-    if (live) {
+    if (live && FORA_IN_RANGE(b.err, pos + ce, total)) {
       const unsigned long long slot = i / (unsigned long long)g.n;
       const unsigned long long v = i - slot * (unsigned long long)g.n;
       b.wr_entry[pos + ce] = (slot << 32) | v;
@@ -357,13 +357,17 @@ __device__ __forceinline__ uint32_t walk_rest(const GraphDev& g, uint4 blk, int 
 // the product is below d (a try Lemire's method may reject; walk_rest decides it, with
 // rb, d and m left for it), else x becomes the chosen out-neighbour.
 __device__ __forceinline__ bool fast_move(const GraphDev& g, uint32_t u, uint32_t& x,
-                                          uint32_t& rb, uint32_t& d, unsigned long long& m) {
+                                          uint32_t& rb, uint32_t& d, unsigned long long& m,
+                                          uint32_t* err, bool& bad) {
+  if (!FORA_IN_RANGE(err, x, g.n)) { bad = true; return false; }
   const uint2 r = g.rd[x];
   rb = r.x;
   d = r.y;
   m = (unsigned long long)u * d;
   if ((uint32_t)m < d) return false;
-  x = walk_target(g, rb + (uint32_t)(m >> 32));
+  const uint32_t e = rb + (uint32_t)(m >> 32);
+  if (!FORA_IN_RANGE(err, e, g.m)) { bad = true; return false; }
+  x = walk_target(g, e);
   return true;
 }
 
@@ -414,7 +418,8 @@ __device__ __forceinline__ void start_walk(const BatchDev& b, const unsigned lon
     w.wgt = sc.wgt[e];
     w.j = (uint32_t)(cbeg + w.i - sc.off[e]);
   } else {
-    const unsigned long long idx = idx0 + e;
+    unsigned long long idx = idx0 + e;
+    if (!FORA_IN_RANGE(b.err, idx, b.totals[0])) idx = idx0;
     const unsigned long long entry = b.wr_entry[idx];
     w.slot = (uint32_t)(entry >> 32);
     w.v = (uint32_t)entry;
@@ -435,22 +440,23 @@ __device__ __forceinline__ void start_walk(const BatchDev& b, const unsigned lon
 // false and capped when it ran into the step cap.
 template <bool kZeroHop>
 __device__ __forceinline__ bool walk_block(const GraphDev& g, uint4 o, uint2 key, uint32_t t_alpha,
-                                           Walk& w, bool& capped) {
+                                           Walk& w, bool& capped, uint32_t* err) {
   bool stop = false;
   uint32_t rb = 0, d = 0;
   unsigned long long m = 0;
   int rejected = -1;  // word index of a try that walk_rest has to decide
+  bool bad = false;   // a failed index check (FORA_DEBUG builds): the walk is dropped
   const uint32_t u0 = kZeroHop ? 0u : o.x, mv0 = kZeroHop ? o.x : o.y;
   const uint32_t t1 = kZeroHop ? o.y : o.z, mv1 = kZeroHop ? o.z : o.w;
   if (!kZeroHop) stop = u0 < t_alpha;
   if (!stop) {
     if (w.steps >= kMaxSteps) { capped = true; w.have = false; return false; }
-    if (fast_move(g, mv0, w.x, rb, d, m)) {
+    if (fast_move(g, mv0, w.x, rb, d, m, err, bad)) {
       ++w.steps;
       stop = t1 < t_alpha;
       if (!stop) {
         if (w.steps >= kMaxSteps) { capped = true; w.have = false; return false; }
-        if (fast_move(g, mv1, w.x, rb, d, m)) {
+        if (fast_move(g, mv1, w.x, rb, d, m, err, bad)) {
           ++w.steps;
           if (kZeroHop) stop = o.w < t_alpha;
         } else {
@@ -461,6 +467,7 @@ __device__ __forceinline__ bool walk_block(const GraphDev& g, uint4 o, uint2 key
       rejected = kZeroHop ? 0 : 1;
     }
   }
+  if (bad) { w.have = false; return false; }
   if (rejected >= 0) {  // rare: decide the try and finish the walk word by word
     const uint32_t end = walk_rest(g, o, rejected + 1, w.cb, w.j, w.v, w.s, key, t_alpha, w.x,
                                    rb, d, m, &w.steps);
@@ -480,7 +487,7 @@ __device__ __forceinline__ void finish_walk(const BatchDev& b, unsigned long lon
   // its end in a walk index (Section 3.3)
   if (b.walk_dest) {
     b.walk_dest[cbeg + w.i] = w.x;
-  } else {
+  } else if (FORA_IN_RANGE(b.err, w.x, n) && FORA_IN_RANGE(b.err, w.slot, b.nsrc)) {
     Tally* t = b.tally + (unsigned long long)w.slot * n + w.x;
     if (b.want_count) atomicAdd(&t->cnt, 1u);
     atomicAdd(&t->acc, w.wgt);
@@ -542,7 +549,7 @@ __global__ void __launch_bounds__(kWalkThreads, kMinBlocks) k_walks(GraphDev g, 
       if (w.have) {
         const uint4 o = philox_rk(make_uint4(w.cb, w.j, w.v, w.s), b.round_key);
         ++w.cb;
-        stop = walk_block<kZeroHop>(g, o, key, t_alpha, w, capped);
+        stop = walk_block<kZeroHop>(g, o, key, t_alpha, w, capped, b.err);
       }
       const bool ended = w.have && stop;
       const uint32_t ends = __ballot_sync(kFull, ended);

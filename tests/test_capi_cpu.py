@@ -103,3 +103,13 @@ def test_workspace_bytes_counts_every_per_query_buffer(lib):
 def test_fail_alloc_hook_arguments(lib):
     assert lib.fora_debug_fail_alloc(-1) == fora.FORA_ERR_BAD_ARG
     assert lib.fora_debug_fail_alloc(0) == fora.FORA_OK
+
+
+def test_debug_build_has_index_checks_and_the_normal_build_not(lib):
+    """FORA_DEBUG builds (device index checks, FORA_ERR_BOUNDS) are a separate library;
+    fora_debug_checks says which one is loaded (host only, no device call)."""
+    import ctypes
+    assert lib.fora_debug_checks() == 0
+    dbg = ctypes.CDLL(fbuild.build(debug=True))
+    assert dbg.fora_debug_checks() == 1
+    assert fora.header_functions() and all(hasattr(dbg, n) for n in fora.header_functions())

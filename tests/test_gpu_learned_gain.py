@@ -38,6 +38,9 @@ def test_learned_rmax_gains_over_the_rule_and_stays_accurate():
     res = lr.evaluate(g, model, ev, params, coef, batch=256)
     print("learned r_max on held-out sources:", res)
     assert res["cost_gain"] > 0.0
+    # measured on the device: the learned r_max is not slower than the rule beyond timing
+    # noise (the modelled gain is a few percent on this small graph)
+    assert res["time_gain"] > -0.03
     # accuracy re-checked on the device's own learned queries of held-out sources (Lemma
     # (layerppr-conc) holds for any r_max): with k = 4096 every returned estimate of a node
     # with pi >= delta is within relative error eps, and every node with pi >= delta left

@@ -43,3 +43,39 @@ def test_results_are_the_same_alone_and_in_the_mix():
         if differ.any():  # only between estimates that are equal within the tolerance
             assert np.all(np.abs(vals[differ] - vals1[differ]) <= 2 * ATOL_PUSH)
     server.close()
+
+
+def test_arrivals_join_running_batches_and_match_the_query_alone():
+    """Requests arriving while a lane's batch is in its push rounds take free slots of that
+    batch between two rounds: such a request finishes with a batch that had already started
+    before it arrived (instead of waiting for the next one), and its result is the same as
+    the query alone (values within the push tolerance, same walk count)."""
+    import time
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    fbuild.build()
+    g = fora.Graph(*inputs.rmat_csr(20, 16, 2))
+    server = fora.Server([g], lanes_per_graph=1, max_batch=64, memory_budget_bytes=16 << 30,
+                         batch_window_ms=0.0, admit_during_push=True)
+    p = fora.Params.make(eps=0.5, k=50, seed=21)
+    src = inputs.uniform_sources(g.n, 120, 2024)
+    tickets = []
+    for s in src:  # arrivals spread over about 60 ms, several batches' push rounds
+        tickets.append(server.submit(0, int(s), p))
+        time.sleep(0.0005)
+    results = [server.wait(t, 50) for t in tickets]
+    st = server.stats()
+    assert st["completed"] == len(src) and st["joined"] >= 1
+    infos = [info for _, _, info in results]
+    joined = [i for i, info in enumerate(infos) if info.joined]
+    assert len(joined) == st["joined"]
+    for j in joined:  # it finished with a batch that had started before it was submitted
+        J = infos[j]
+        assert any(R.start_ms < J.submit_ms and R.end_ms == J.end_ms and not R.joined
+                   for R in infos)
+    for s, (ids, vals, info) in zip(src, results):
+        ids1, vals1, st1 = g.ssppr(int(s), p)
+        np.testing.assert_allclose(vals, vals1, rtol=0, atol=ATOL_PUSH)
+        assert info.stats.walks == st1.walks and info.stats.pushes == st1.pushes
+    server.close()
+    g.close()

@@ -135,21 +135,31 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def profiled_traffic(kernel, wl, launches_per_step=1):
-    """DRAM bytes per launch from a committed ncu summary (profiles/<kernel>_<wl>.txt,
-    lines 'dram_bytes_per_launch: <int>' and 'launches_per_step: <int>'), or None when
-    there is none or it was taken with another split of the step into launches."""
+def profile_values(kernel, wl):
+    """'key: value' lines of a committed ncu summary (profiles/<kernel>_<wl>.txt), {} if
+    there is none."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{wl}.txt")
-    found, split = None, 1
+    out = {}
     try:
         for line in open(path):
-            if line.startswith("dram_bytes_per_launch:"):
-                found = int(float(line.split(":", 1)[1]))
-            elif line.startswith("launches_per_step:"):
-                split = int(line.split(":", 1)[1])
-    except Exception:
+            if ":" in line and not line.startswith(" ") and not line.startswith("#"):
+                key, val = line.split(":", 1)
+                try:
+                    out[key.strip()] = float(val.split()[0])
+                except (ValueError, IndexError):
+                    pass
+    except OSError:
+        return {}
+    return out
+
+
+def profiled_traffic(kernel, wl, launches_per_step=1, key="dram_bytes_per_launch"):
+    """DRAM bytes per launch (or per step, with key) from a committed ncu summary, or None
+    when there is none or it was taken with another split of the step into launches."""
+    v = profile_values(kernel, wl)
+    if key not in v or int(v.get("launches_per_step", 1)) != launches_per_step:
         return None
-    return found if split == launches_per_step else None
+    return int(v[key])
 
 
 def oracle_threads():
@@ -367,6 +377,38 @@ def run_fora(args):
     if mode == "learned":
         rule_ms = timed(None, args.steps)
         comparison["batched_rule_qps"] = B * args.steps / (sum(rule_ms) / 1e3)
+        # the learned model's comparators, with the constant multiple and the per-unit costs
+        # its training run chose on this workload (models/rmax_<workload>.json): a constant
+        # multiple of the rule's r_max, and the balanced push of Section 4.2 (Alg. 3)
+        report_path = os.path.splitext(model_path)[0] + ".json"
+        if os.path.exists(report_path):
+            rep = json.load(open(report_path))
+            r_rule = g.resolve(params)[0]
+            cmult = float(rep["constant"]["chosen"])
+            bc = rep["balance_costs_ms"]
+            costs = (bc["edge_push"], bc["push"], bc["walk"])
+            arms = {
+                "constant": lambda src: g.ssppr_batch_rmax(src, [r_rule * cmult] * len(src), params,
+                                                           out_ids=ids, out_vals=vals,
+                                                           stream=stream),
+                "balanced": lambda src: g.ssppr_batch_balanced(src, params, costs, out_ids=ids,
+                                                               out_vals=vals, stream=stream)}
+            for name, fn in arms.items():
+                fn(sources(-77))
+                tot = 0.0
+                for step in range(args.steps):
+                    src = sources(step)
+                    flush.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    fn(src)
+                    e1.record(stream)
+                    e1.synchronize()
+                    tot += e0.elapsed_time(e1)
+                comparison[f"batched_{name}_qps"] = B * args.steps / (tot / 1e3)
+            comparison["constant_multiple"] = cmult
+            comparison["balance_costs_ms"] = bc
     if args.plain_sources > 0:
         # plain FORA: one query at a time through fora_ssppr (rule r_max, host results),
         # each query's latency on the host clock around the synchronous call
@@ -442,11 +484,20 @@ def run_fora(args):
                 "traffic": profiled_traffic("k_walks", args.workload, launches_per_step),
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "launches_per_step": launches_per_step}
+    # the walk kernel is bound by issue and latency rather than by DRAM: its issue-slot and
+    # L2 fractions from the committed ncu section capture of the same kernel (64 sources)
+    wp = profile_values("k_walks", args.workload)
+    if "issue_active_frac" in wp:
+        roofline["issue_frac"] = wp["issue_active_frac"]
+        roofline["l2_frac"] = wp.get("lts_throughput_frac")
+        roofline["issue_l2_source"] = "ncu section capture, profiles/k_walks_" + args.workload + ".txt"
     # the push phase (all its rounds: spread, take, advance) against the same peak
     achieved_push = (sum(push_bytes) / len(push_bytes)) / (statistics.mean(push_ms) / 1e3) / 1e9
     roofline_push = {"bound": "hbm", "kernels": "k_push_spread+k_push_take+k_push_advance",
                      "achieved": achieved_push, "peak": peak, "peak_kind": peak_kind,
-                     "unit": "GB/s", "frac": achieved_push / peak, "traffic": None,
+                     "unit": "GB/s", "frac": achieved_push / peak,
+                     "traffic": profiled_traffic("push", args.workload, 1, "dram_bytes_per_step"),
+                     "traffic_unit": "bytes per step (all push launches)",
                      "algorithmic_bytes_per_step": sum(push_bytes) / len(push_bytes)}
 
     cpu = None

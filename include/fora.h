@@ -133,7 +133,7 @@ typedef struct {
  * m = row_ptr[n] < 2^32 and d_out(v) >= 1 for every v (FORA_ERR_DANGLING: a walk of
  * Section 2.1 needs an out-neighbour at every node).  Edges are taken with
  * multiplicity; self-loops are allowed.  flags: 0.  Device memory: about
- * 4 (n + 1) + 4 m + 16 n bytes, plus a bit-packed copy of col for the walks when
+ * 4 (n + 1) + 4 m + 20 n bytes, plus a bit-packed copy of col for the walks when
  * ceil(log2 n) <= 24.  Errors: FORA_ERR_BAD_ARG, FORA_ERR_DANGLING, FORA_ERR_OOM,
  * FORA_ERR_CUDA (no device); *out is NULL on any error.
  */

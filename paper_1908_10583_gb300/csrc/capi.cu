@@ -116,6 +116,9 @@ fora::WorkspaceSizes fora::workspace_sizes(int64_t n, uint64_t hub_chunks, int n
   z.rmax = S * sizeof(double);
   z.stats = S * sizeof(SlotStats);
   z.stopped = S * sizeof(uint32_t);
+  z.light = S;
+  z.tile_dirty = S * (((size_t)n + kTakeTile - 1) / kTakeTile);
+  z.last_edges = S * sizeof(unsigned long long);
   z.blk = 2 * (size_t)kMaxResidualGrid * sizeof(unsigned long long);
   z.topk = topk_scratch_bytes(nsrc);
   z.feat = S * FORA_NUM_FEATURES * sizeof(float);
@@ -128,8 +131,8 @@ fora::WorkspaceSizes fora::workspace_sizes(int64_t n, uint64_t hub_chunks, int n
 
 size_t fora::WorkspaceSizes::total() const {
   return r + res + tally + 2 * q + fa + 2 * hub + small + work + alist + slot_cnt + pre + ps +
-         err + sources + rmax + stats + stopped + blk + topk + feat + pred + rmax_learned +
-         out_ids + out_vals;
+         err + sources + rmax + stats + stopped + light + tile_dirty + last_edges + blk + topk +
+         feat + pred + rmax_learned + out_ids + out_vals;
 }
 
 namespace {
@@ -168,6 +171,9 @@ int ensure_workspace(fora_graph* g, Workspace* w, int nsrc) {
   CUDA_TRY(dalloc(&w->rmax, z.rmax));
   CUDA_TRY(dalloc(&w->stats, z.stats));
   CUDA_TRY(dalloc(&w->stopped, z.stopped));
+  CUDA_TRY(dalloc(&w->light, z.light));
+  CUDA_TRY(dalloc(&w->tile_dirty, z.tile_dirty));
+  CUDA_TRY(dalloc(&w->last_edges, z.last_edges));
   CUDA_TRY(dalloc(&w->blk, z.blk));
   CUDA_TRY(dalloc(&w->topk_scratch, z.topk));
   CUDA_TRY(dalloc(&w->feat, z.feat));
@@ -401,6 +407,12 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
   b.residual_grid = w->residual_grid;
   b.theta = w->rmax;
   b.stopped = w->stopped;
+  b.light = w->light;
+  b.tile_dirty = w->tile_dirty;
+  b.last_edges = w->last_edges;
+  b.tiles = ((unsigned long long)g->n + kTakeTile - 1) / kTakeTile;
+  // a frontier whose spread touches at most about half of a source's tiles
+  b.light_edges = b.tiles / 2;
   if (bal) {
     b.balance = 1;
     b.bal_scale = b.zero_hop ? (1.0 - rp.alpha) * rp.walk_scale : rp.walk_scale;
@@ -431,6 +443,8 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
     CUDA_TRY(cudaMemsetAsync(w->res, 0, N * sizeof(double), stream));
     CUDA_TRY(cudaMemsetAsync(w->work, 0, 32 * sizeof(unsigned long long), stream));
     CUDA_TRY(cudaMemsetAsync(w->slot_cnt, 0, 4 * (size_t)w->cap * sizeof(uint32_t), stream));
+    CUDA_TRY(cudaMemsetAsync(w->tile_dirty, 0, (size_t)w->cap * b.tiles, stream));
+    CUDA_TRY(cudaMemsetAsync(w->last_edges, 0, (size_t)w->cap * sizeof(unsigned long long), stream));
     CUDA_TRY(launch_push_seed(gd, b, stream));
     if (join) {
       // rounds from a host loop; after each round further sources may join as new slots

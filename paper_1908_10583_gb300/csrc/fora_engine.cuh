@@ -10,6 +10,9 @@ namespace fora {
 // Nodes with more out-edges than this are pushed in chunks of this many edges,
 // one warp per chunk, so that a hub never serialises a round on one warp.
 constexpr uint32_t kHubChunk = 256;
+
+// Nodes of one source a warp of the push take scans as one tile.
+constexpr uint32_t kTakeTile = 1024;
 constexpr int kHubChunkBits = 24;  // hub item = (frontier index << 24) | chunk
 
 // Top-k radix select: 96-bit keys (estimate bits : ~id), 12-bit digits.
@@ -160,6 +163,16 @@ struct BatchDev {
   double bal_scale, cost_edge, cost_push, cost_walk;
   double* theta;       // [nsrc] the thresholds (the same array as rmax)
   uint32_t* stopped;   // [nsrc] 1 once the cost rule stopped the source's push
+  // Light rounds: after every take each node of an active source is at or below its
+  // threshold, so only nodes the next spread adds to can cross.  When a source's new
+  // frontier spreads fewer than light_edges edges, light[s] = 1: its spread marks the
+  // kTakeTile-node tiles it touches in tile_dirty and its take scans only those (clearing
+  // them); otherwise the take scans every tile.
+  uint8_t* light;                  // [nsrc]
+  uint8_t* tile_dirty;             // [nsrc][tiles]
+  unsigned long long* last_edges;  // [nsrc] the source's edge pushes at the last advance
+  unsigned long long tiles;        // tiles per source, ceil(n / kTakeTile)
+  unsigned long long light_edges;
 };
 
 // Launch-shape parameters of a graph (set through fora_graph_tune or the autotuner).

@@ -34,7 +34,7 @@ namespace {
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kTakeThreads = 256;
 constexpr int kSpreadThreads = 256;
-constexpr uint32_t kTileNodes = 1024;  // nodes of one source a warp scans per take tile
+constexpr uint32_t kTileNodes = kTakeTile;  // nodes of one source a warp scans per take tile
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
@@ -130,6 +130,9 @@ __global__ void k_push_seed(GraphDev g, BatchDev b) {
     const uint32_t src = (uint32_t)b.sources[slot];
     b.r[(unsigned long long)slot * (unsigned long long)g.n + src] = 1.0;
     b.alist[slot] = (uint32_t)slot;
+    // only r(s) is non-zero: the first take scans the source's tile alone
+    b.light[slot] = 1;
+    b.tile_dirty[(unsigned long long)slot * b.tiles + src / kTileNodes] = 1;
     if (b.balance) {
       // the cost rule before any push: FC = 0 against the walk cost of r_sum = 1
       const bool stop = 0.0 >= __dmul_rn(__dmul_rn(1.0, b.bal_scale), b.cost_walk);
@@ -197,6 +200,7 @@ __global__ void __launch_bounds__(kSpreadThreads, 6) k_push_spread(GraphDev g, B
   int cs = 0;                           // source of the cached range
   unsigned long long clo = 1, chi = 0;  // its groups [clo, chi) (empty: nothing cached)
   uint32_t ccnt = 0;
+  bool clight = false;                  // the cached source's round is light: mark tiles
   for (;;) {
     unsigned long long v0 = 0;
     if (lane == 0) v0 = atomicAdd(&b.work[0], kGrab);
@@ -211,6 +215,7 @@ __global__ void __launch_bounds__(kSpreadThreads, 6) k_push_spread(GraphDev g, B
         clo = b.gpre[cs];
         chi = b.gpre[cs + 1];
         ccnt = cnt[cs];
+        clight = b.light[cs] != 0;
       }
       const uint32_t i = (uint32_t)(grp - clo) * 32u + lane;
       const unsigned long long base_gi = (unsigned long long)cs * n;
@@ -251,6 +256,12 @@ __global__ void __launch_bounds__(kSpreadThreads, 6) k_push_spread(GraphDev g, B
 #pragma unroll
         for (int k = 0; k < 4; ++k)
           spread_slice(b.r, base_gi, u[k], own[k], ik[k], act[k], b.err, n);
+        if (clight) {  // warp-uniform
+          uint8_t* dirty = b.tile_dirty + (unsigned long long)cs * b.tiles;
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (act[k] && u[k] < n) dirty[u[k] / kTileNodes] = 1;
+        }
       }
     }
   }
@@ -273,6 +284,7 @@ __global__ void __launch_bounds__(kSpreadThreads, 6) k_push_spread(GraphDev g, B
         cs = slot_of(b.hpre, b.nsrc, h);
         clo = b.hpre[cs];
         chi = b.hpre[cs + 1];
+        clight = b.light[cs] != 0;
       }
       const unsigned long long item =
           b.hub[cur][(unsigned long long)cs * b.hub_stride + (h - clo)];
@@ -293,6 +305,12 @@ __global__ void __launch_bounds__(kSpreadThreads, 6) k_push_spread(GraphDev g, B
 #pragma unroll
       for (int k = 0; k < (int)(kHubChunk / 32); ++k)
         spread_slice(b.r, gbase, u[k], 0u, inc, u[k] != 0xFFFFFFFFu, b.err, n);
+      if (clight) {  // warp-uniform
+        uint8_t* dirty = b.tile_dirty + (unsigned long long)cs * b.tiles;
+#pragma unroll
+        for (int k = 0; k < (int)(kHubChunk / 32); ++k)
+          if (u[k] < n) dirty[u[k] / kTileNodes] = 1;
+      }
     }
   }
 }
@@ -325,6 +343,12 @@ __global__ void __launch_bounds__(kTakeThreads, 3) k_push_take(GraphDev g, Batch
   for (unsigned long long t = blockIdx.x * wpb + (threadIdx.x >> 5); t < ntiles; t += nwarps) {
     const uint32_t s = b.alist[t / tps];
     if (b.balance && b.stopped[s]) continue;  // warp-uniform: stopped before its first push
+    if (b.light[s]) {  // warp-uniform: only the tiles this round's spread added to
+      uint8_t* flag = b.tile_dirty + (unsigned long long)s * b.tiles + t % tps;
+      if (*flag == 0) continue;
+      __syncwarp();
+      if (lane == 0) *flag = 0;
+    }
     const uint32_t tb = (uint32_t)((t % tps) * kTileNodes);
     const double rm = b.rmax[s];
     const float rmf = __double2float_rn(rm);
@@ -493,6 +517,15 @@ __global__ void __launch_bounds__(1024) k_push_advance(BatchDev b,
       }
     }
     if (s < nsrc && c > 0) b.stats[s].rounds += 1u;  // a push round of this source
+    if (s < nsrc) {
+      // the frontier just taken is spread next; a light one lets the next take scan only
+      // the tiles it touches (a halved threshold needs a full scan)
+      const unsigned long long ep = b.stats[s].edge_pushes;
+      const unsigned long long round_edges = ep - b.last_edges[s];
+      b.last_edges[s] = ep;
+      const bool halved = b.balance && take && c == 0;
+      b.light[s] = (take && !halved && round_edges < b.light_edges) ? 1 : 0;
+    }
     unsigned long long ge, he, gt, ht, ae, ze, at, zt;
     block_scan2((c + 31u) / 32u, h, &ge, &he, &gt, &ht);
     block_scan2(take ? 1u : 0u, 0u, &ae, &ze, &at, &zt);
@@ -540,8 +573,11 @@ __global__ void k_push_join(GraphDev g, BatchDev b, int first, int k) {
   const uint32_t nact = ps->nact;
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
     const int slot = first + i;
-    b.r[(unsigned long long)slot * (unsigned long long)g.n + (uint32_t)b.sources[slot]] = 1.0;
+    const uint32_t src = (uint32_t)b.sources[slot];
+    b.r[(unsigned long long)slot * (unsigned long long)g.n + src] = 1.0;
     b.alist[nact + i] = (uint32_t)slot;
+    b.light[slot] = 1;
+    b.tile_dirty[(unsigned long long)slot * b.tiles + src / kTileNodes] = 1;
     b.gpre[slot + 1] = gtot;
     b.hpre[slot + 1] = htot;
   }

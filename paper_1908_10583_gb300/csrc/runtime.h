@@ -23,7 +23,7 @@ struct WorkspaceSizes {
   size_t N = 0;  // nsrc * n
   size_t r = 0, res = 0, tally = 0, q = 0, fa = 0, hub = 0, small = 0, work = 0, alist = 0,
          slot_cnt = 0, pre = 0, ps = 0, err = 0, sources = 0, rmax = 0, stats = 0, stopped = 0,
-         blk = 0,
+         light = 0, tile_dirty = 0, last_edges = 0, blk = 0,
          topk = 0, feat = 0, pred = 0, rmax_learned = 0, out_ids = 0, out_vals = 0;
   size_t total() const;  // q and hub count twice (two parities)
 };
@@ -74,6 +74,9 @@ struct Workspace {
   double* rmax = nullptr;
   SlotStats* stats = nullptr;
   uint32_t* stopped = nullptr;        // [nsrc] balanced push: the cost rule stopped the source
+  uint8_t* light = nullptr;           // [nsrc] light-round flags of the push take
+  uint8_t* tile_dirty = nullptr;      // [nsrc][tiles] tiles a light round's spread touched
+  unsigned long long* last_edges = nullptr;  // [nsrc]
   unsigned long long* blk = nullptr;  // [2][residual_grid]
   int residual_grid = 0;
   void* topk_scratch = nullptr;
@@ -104,7 +107,7 @@ struct Workspace {
     dfree(ps);
     dfree(r); dfree(res); dfree(tally);
     dfree(q[0]); dfree(q[1]); dfree(hub[0]); dfree(hub[1]); dfree(fa);
-    dfree(small); dfree(work); dfree(alist); dfree(slot_cnt); dfree(pre); dfree(err); dfree(sources); dfree(rmax); dfree(stats); dfree(stopped); dfree(blk);
+    dfree(small); dfree(work); dfree(alist); dfree(slot_cnt); dfree(pre); dfree(err); dfree(sources); dfree(rmax); dfree(stats); dfree(stopped); dfree(light); dfree(tile_dirty); dfree(last_edges); dfree(blk);
     if (topk_scratch) cudaFree(topk_scratch);
     topk_scratch = nullptr;
     dfree(out_ids); dfree(out_vals); dfree(feat); dfree(pred); dfree(rmax_learned);

@@ -72,9 +72,24 @@ __global__ void __launch_bounds__(256) k_topk_hist(const double* __restrict__ es
   int64_t beg, end;
   row_range(n, blockIdx.x, gridDim.x, &beg, &end);
   const double* e = est + (size_t)row * (size_t)n;
-  for (int64_t t = beg + threadIdx.x; t < end; t += blockDim.x) {
-    const u128 z = key_of(e[t], (uint32_t)t);
-    if ((z >> (96 - s.plen)) == p) atomicAdd(&sh[(uint32_t)(z >> shift_digit) & (kBins - 1)], 1u);
+  const uint32_t lane = threadIdx.x & 31;
+  // keys crowd into few bins (every zero estimate, and the few binades the others span, share
+  // the leading digits), so the lanes of a warp that fall into the same bin add their count
+  // once (their lowest lane), instead of serialising on one shared-memory counter
+  for (int64_t base = beg; base < end; base += blockDim.x) {
+    const int64_t t = base + threadIdx.x;
+    bool in = false;
+    uint32_t bin = 0;
+    if (t < end) {
+      const u128 z = key_of(e[t], (uint32_t)t);
+      in = (z >> (96 - s.plen)) == p;
+      bin = (uint32_t)(z >> shift_digit) & (kBins - 1);
+    }
+    const unsigned members = __ballot_sync(0xFFFFFFFFu, in);
+    if (in) {
+      const unsigned grp = __match_any_sync(members, bin);
+      if ((grp & ((1u << lane) - 1u)) == 0) atomicAdd(&sh[bin], (uint32_t)__popc(grp));
+    }
   }
   __syncthreads();
   uint32_t* h = hist + (size_t)row * kBins;

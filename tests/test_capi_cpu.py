@@ -79,8 +79,8 @@ def test_workspace_bytes_counts_every_per_query_buffer(lib):
     allocates and the serving lanes admit by.  Per query slot, counted by hand from the
     layout: residue, reserve (8 B each), walk tally (16 B), two frontier queues and the
     increments (8 B each) per node; two hub-item lists (8 B per hub chunk); per-source
-    state (alist 4, counters 16, prefixes 16, source 4, r_max 8, stats 64, stop flag 4);
-    top-k scratch
+    state (alist 4, counters 16, prefixes 16, source 4, r_max 8, stats 64, stop flag 4,
+    light-round flag 1, edge count 8, one byte per 1024-node tile); top-k scratch
     (4096 histogram bins of 4 B, 32 B select state, 8192 candidates of 12 B); features
     64, prediction 4, learned r_max 8; staged results 4096 x (4 + 8)."""
     import inputs
@@ -88,7 +88,7 @@ def test_workspace_bytes_counts_every_per_query_buffer(lib):
     n = len(rp) - 1
     deg = (rp[1:] - rp[:-1]).astype(int)
     hub_chunks = int(sum((d + 255) // 256 for d in deg if d > 256))
-    per = (56 * n + 2 * 8 * hub_chunks + (4 + 16 + 16 + 4 + 8 + 64 + 4)
+    per = (56 * n + 2 * 8 * hub_chunks + (4 + 16 + 16 + 4 + 8 + 64 + 4 + 1 + 8 + (n + 1023) // 1024)
            + (4096 * 4 + 32 + 8192 * 12) + (64 + 4 + 8) + 4096 * 12)
     b = [fora.workspace_bytes(rp, s) for s in (1, 2, 3, 64)]
     assert b[1] - b[0] == per and b[2] - b[1] == per

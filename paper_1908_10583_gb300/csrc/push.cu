@@ -157,6 +157,11 @@ __global__ void k_push_seed(GraphDev g, BatchDev b) {
   }
 }
 
+// 0, 1, ..., 32 as FP64 (the run lengths of spread_slice).
+__constant__ double kMultiple[33] = {0,  1,  2,  3,  4,  5,  6,  7,  8,  9,  10,
+                                     11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21,
+                                     22, 23, 24, 25, 26, 27, 28, 29, 30, 31, 32};
+
 // r[base + u] += inc for the active lanes of one 32-edge slice whose lanes hold consecutive
 // CSR entries (lane order = entry order; inactive lanes only at the end).  Rows are
 // sorted, so the copies of a multi-edge (v, u) are adjacent: a run of lanes with the same
@@ -171,11 +176,19 @@ __device__ __forceinline__ void spread_slice(double* r, unsigned long long base,
   const uint32_t po = __shfl_up_sync(kFull, owner, 1);
   const bool cont = act && lane > 0 && pu == u && po == owner;  // continues lane - 1's run
   const uint32_t brk = __ballot_sync(kFull, !cont);              // run starts and idle lanes
-  if (act && !cont && FORA_IN_RANGE(err, u, n)) {
+  const bool lead = act && !cont;
+  uint32_t k = 1;
+  if (lead) {
     const uint32_t above = brk & ~((2u << lane) - 1u);
-    const uint32_t k = (above ? (uint32_t)__ffs(above) - 1u : 32u) - lane;
-    atomicAdd(&r[base + u], k == 1u ? inc : __dmul_rn(inc, (double)k));
+    k = (above ? (uint32_t)__ffs(above) - 1u : 32u) - lane;
   }
+  // FP64 arithmetic only in slices that hold a run (this GPU's FP64 rate is low, and most
+  // slices have none); kMultiple[k] = k avoids an integer-to-FP64 conversion
+  double add = inc;
+  if (__any_sync(kFull, k > 1u)) {
+    if (k > 1u) add = __dmul_rn(inc, kMultiple[k]);
+  }
+  if (lead && FORA_IN_RANGE(err, u, n)) atomicAdd(&r[base + u], add);
 }
 
 // Work is handed out dynamically (kGrab groups or hub items per atomic), so the warps

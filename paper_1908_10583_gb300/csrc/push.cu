@@ -196,7 +196,10 @@ __device__ __forceinline__ void spread_slice(double* r, unsigned long long base,
 // of each group.
 constexpr unsigned long long kGrab = 4;
 
-__global__ void __launch_bounds__(kSpreadThreads, 6) k_push_spread(GraphDev g, BatchDev b) {
+#ifndef FORA_SPREAD_MIN_BLOCKS
+#define FORA_SPREAD_MIN_BLOCKS 6
+#endif
+__global__ void __launch_bounds__(kSpreadThreads, FORA_SPREAD_MIN_BLOCKS) k_push_spread(GraphDev g, BatchDev b) {
   const int cur = b.ps->cur;
   const unsigned long long ngroups = b.ps->ngroups;
   const unsigned long long nh = b.ps->nhub;
@@ -333,7 +336,13 @@ __global__ void __launch_bounds__(kSpreadThreads, 6) k_push_spread(GraphDev g, B
 // residues and both row offsets are loaded before any is used, the crossing nodes of
 // the 8 words are counted, one atomic per counter reserves their places in the source's
 // queue region, and the crossing nodes are taken.
-__global__ void __launch_bounds__(kTakeThreads, 3) k_push_take(GraphDev g, BatchDev b) {
+// Resident blocks per SM the take and the spread are compiled for (measured on the 2^20
+// graph, 256 sources: take 3 -> 4 blocks 120.4 -> 118.5 ms of push; spread 7 or 8 blocks
+// instead of 6 made it slower, 128-130 ms: more scattered reductions in flight contend at L2).
+#ifndef FORA_TAKE_MIN_BLOCKS
+#define FORA_TAKE_MIN_BLOCKS 4
+#endif
+__global__ void __launch_bounds__(kTakeThreads, FORA_TAKE_MIN_BLOCKS) k_push_take(GraphDev g, BatchDev b) {
   const PushState* ps = b.ps;
   const int nx = ps->cur ^ 1;
   const unsigned long long n = (unsigned long long)g.n;

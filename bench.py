@@ -409,6 +409,23 @@ def run_fora(args):
                 comparison[f"batched_{name}_qps"] = B * args.steps / (tot / 1e3)
             comparison["constant_multiple"] = cmult
             comparison["balance_costs_ms"] = bc
+    # the same batches with zero-hop pruning (Section 4.1: alpha of every residue goes to the
+    # estimate directly and each walk starts with a forced move), rule r_max
+    zparams = fora.Params.from_buffer_copy(params)
+    zparams.flags |= fora.FORA_ZERO_HOP
+    g.ssppr_batch(sources(-78), zparams, out_ids=ids, out_vals=vals, stream=stream)
+    ztot = 0.0
+    for step in range(args.steps):
+        src = sources(step)
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.ssppr_batch(src, zparams, out_ids=ids, out_vals=vals, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        ztot += e0.elapsed_time(e1)
+    comparison["batched_zero_hop_rule_qps"] = B * args.steps / (ztot / 1e3)
     if args.plain_sources > 0:
         # plain FORA: one query at a time through fora_ssppr (rule r_max, host results),
         # each query's latency on the host clock around the synchronous call

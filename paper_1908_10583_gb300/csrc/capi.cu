@@ -1,6 +1,7 @@
 // C ABI (include/fora.h) and the host side of the query engine: graph residency,
 // the per-graph workspace, and the phase sequence of a (batched) query.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <atomic>
@@ -136,6 +137,24 @@ size_t fora::WorkspaceSizes::total() const {
 }
 
 namespace {
+
+// NVTX ranges (shown by profilers that record them, no effect otherwise): one per batched
+// call, and one per phase inside it; `next` closes the open phase and opens another.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+struct NvtxPhases {
+  bool open = false;
+  void next(const char* name) {
+    if (open) nvtxRangePop();
+    nvtxRangePushA(name);
+    open = true;
+  }
+  ~NvtxPhases() {
+    if (open) nvtxRangePop();
+  }
+};
 
 template <typename T>
 cudaError_t dalloc(T** p, size_t bytes) {
@@ -431,6 +450,9 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
 
   if (hook && hook->before && hook->before->wait())  // the earlier part's push is done
     CUDA_TRY(cudaStreamWaitEvent(stream, hook->before->ev, 0));
+  NvtxRange nvtx_call("fora: batched query");
+  NvtxPhases nvtx_phase;
+  nvtx_phase.next("fora: push");
   const bool timed = st != nullptr;
   if (timed) CUDA_TRY(cudaEventRecord(w->ev[0], stream));
 
@@ -505,6 +527,7 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
   }
 
   // ---- walks (Alg. 2) ----
+  nvtx_phase.next("fora: walks");
   CUDA_TRY(launch_residuals(gd, b, stream));
   if (timed) CUDA_TRY(cudaEventRecord(w->ev[2], stream));
   if (indexed)
@@ -517,6 +540,7 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
                                  g->num_sms, stream));
 
   // ---- estimate and top-k (the residue array becomes the estimate) ----
+  nvtx_phase.next("fora: estimate and top-k");
   CUDA_TRY(launch_estimate(w->res, w->tally, w->r, w->r, rp.alpha, b.zero_hop, N, g->num_sms, stream));
   if (dbg && dbg->estimate)
     CUDA_TRY(cudaMemcpyAsync(dbg->estimate, w->r, N * sizeof(double), cudaMemcpyDeviceToDevice, stream));

@@ -13,6 +13,9 @@
 5. comparators: the best constant multiple of the rule (measured on training sources over
    the grid and the paper's r*, 2r*, ..., 7r*, Section 8 "Tuning r_max") and the balanced
    push of Section 4.2 (Alg. 3) with the calibrated costs;
+   anchor: the network's output is moved so that its mean over the training sources is
+   the chosen constant, and its per-source deviations are kept at the share (0, 1/4, 1/2
+   or 1) with the least measured time on the training sources (0: the constant itself);
 6. evaluate: held-out sources, batched, with the rule, the constant, the balanced push and
    the learned r_max: measured time per batch and modelled cost; optionally also on a
    second (larger) graph, whose per-unit costs the balanced push gets from a short
@@ -117,6 +120,49 @@ def labels(costs, mults=MULTS):
             if den > 0:
                 out[i] += 0.5 * (lg[1] - lg[0]) * (y0 - y2) / den
     return np.clip(out, lg[0], lg[-1])
+
+
+# Offsets of the output layer in the model's parameter vector
+# (W1[64][16] | b1[64] | W2[64][64] | b2[64] | W3[64] | b3).
+OFF_W3 = 64 * 16 + 64 + 64 * 64 + 64
+OFF_B3 = OFF_W3 + 64
+
+
+def anchored(params, pred, const_mult, lam):
+    """Output-layer change that anchors the network at a measured constant: the new output
+    is log2(const_mult) + lam * (y - mean y), y the current output and the mean over the
+    training sources (clamped to +-3 as the query clamps it); W3 is scaled by lam (a power
+    of two or 0: exact in BF16) and b3 moved accordingly.  lam = 0 is the constant itself."""
+    p = np.array(params, dtype=np.float32, copy=True)
+    mu = float(np.clip(pred, -3.0, 3.0).mean())
+    p[OFF_W3:OFF_B3] *= np.float32(lam)
+    p[OFF_B3] = np.float32(lam * float(params[OFF_B3]) + (np.log2(const_mult) - lam * mu))
+    return p
+
+
+def select_lambda(g, model, sources, features, params, const_mult, lams=(0.0, 0.25, 0.5, 1.0),
+                  batch=256):
+    """The lam of `anchored` with the least measured time on `sources` (training sources);
+    the model is left at that choice.  -> (lam, {lam: ms})."""
+    torch = _torch()
+    base, norm = model.get()
+    pred = model.predict(features)
+    ids = torch.empty((batch, params.k), dtype=torch.int32, device="cuda")
+    vals = torch.empty((batch, params.k), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    times = {}
+    for lam in lams:
+        model.set(anchored(base, pred, const_mult, lam), norm)
+        ms = 0.0
+        for lo in range(0, len(sources), batch):
+            chunk = sources[lo:lo + batch]
+            ms += _timed(lambda: g.ssppr_batch_learned(chunk, params, model, out_ids=ids[:len(chunk)],
+                                                      out_vals=vals[:len(chunk)], stream=stream),
+                         stream)[0]
+        times[float(lam)] = ms
+    best = min(times, key=times.get)
+    model.set(anchored(base, pred, const_mult, best), norm)
+    return best, times
 
 
 def train(features, target, epochs=80, batch=256, lr=2e-3, seed=0):
@@ -263,6 +309,11 @@ def main(argv=None):
     cands = sorted(set(MULTS.tolist()) | set(PAPER_MULTS.tolist()))
     const_mult, const_times = best_constant(g, tr[:args.const_sources], params, cands,
                                             batch=args.batch)
+    # anchor the network at the measured constant; keep the measured share of its deviations
+    lam, lam_times = select_lambda(g, model, tr[:args.const_sources], x, params, const_mult,
+                                   batch=args.batch)
+    if args.model_out:
+        model.save(args.model_out)
     bal = balance_costs(coef)
     res = evaluate(g, model, ev, params, coef, batch=args.batch, const_mult=const_mult,
                    balance=bal)
@@ -273,6 +324,7 @@ def main(argv=None):
            "best_multiplier_cost_gain_train": float(1 - ycost.min(1).sum() / ycost[:, 3].sum()),
            "constant": {"chosen": const_mult, "ms_on_training_sources": const_times,
                         "sources": min(args.const_sources, len(tr))},
+           "anchor": {"lambda": lam, "ms_on_training_sources": lam_times},
            "balance_costs_ms": {"edge_push": bal[0], "push": bal[1], "walk": bal[2]},
            "loss_first_last": [float(hist[0]), float(hist[-1])], "eval": res,
            "seconds": {"measure": t1 - t0, "train": t2 - t1, "eval": time.time() - t2}}

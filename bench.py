@@ -312,6 +312,8 @@ def run_fora(args):
     if not args.no_autotune and not args.tune:
         # autotuned frontier segments and walk-block shapes on a batch of the workload
         tuning.update(g.autotune(sources(-100), params, stream=stream))
+    tuning["spread_hot"] = g.tuning("spread_hot")
+    tuning["hot_nodes"] = g.tuning("hot_nodes")
     for i in range(args.warmup):
         one_step(sources(-1 - i), model)
     torch.cuda.synchronize()

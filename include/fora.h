@@ -134,7 +134,9 @@ typedef struct {
  * Section 2.1 needs an out-neighbour at every node).  Edges are taken with
  * multiplicity; self-loops are allowed.  flags: 0.  Device memory: about
  * 4 (n + 1) + 4 m + 20 n bytes, plus a bit-packed copy of col for the walks when
- * ceil(log2 n) <= 24.  Errors: FORA_ERR_BAD_ARG, FORA_ERR_DANGLING, FORA_ERR_OOM,
+ * ceil(log2 n) <= 24, plus 4 m bytes of target codes for the push when some node has
+ * in-degree >= 64 (the up to 128 nodes of highest in-degree are marked in them, see
+ * "spread_hot").  Errors: FORA_ERR_BAD_ARG, FORA_ERR_DANGLING, FORA_ERR_OOM,
  * FORA_ERR_CUDA (no device); *out is NULL on any error.
  */
 int fora_graph_create(int64_t n, const int64_t *row_ptr, const int32_t *col, uint32_t flags,
@@ -418,7 +420,13 @@ int fora_threshold_debug(const double *r, const double *rmax, const uint32_t *d,
  * speed):  "spread_width" (1..4096, default 1): the push visits the frontier of a round
  * (grouped by source) through this many interleaved segments, so the warps in flight cover about that
  * many sources at once (wider spreads reductions on shared hub targets over more
- * addresses; narrower keeps the residue arrays in flight smaller).  "walk_blocks" (3, 4
+ * addresses; narrower keeps the residue arrays in flight smaller).  "spread_hot" (0 or 1,
+ * default 1): in the heavy rounds of the push a block first sums, in shared memory, its
+ * pushes to the graph's hot nodes (the up to 128 nodes of highest in-degree, each >= 64)
+ * over a stretch of up to 32 frontier groups of one source, then adds each sum to the
+ * residue with one atomic; 0 adds every push with its own atomic (results differ only by
+ * the order of FP64 additions).  The tuning read-back also answers "hot_nodes", the
+ * number of hot nodes of the graph (0: spread_hot has no effect).  "walk_blocks" (3, 4
  * or 5, default 4): resident walk blocks per SM, traded against registers per thread.
  * "push_host_loop" (0 or 1, default 0): 1 launches the push rounds from a host loop with
  * one device-to-host read per round, instead of the CUDA graph whose conditional while-node

@@ -273,6 +273,7 @@ int push_loop_graph(fora_graph* g, Workspace* w, const GraphDev& gd, const Batch
   key.nsrc = b.nsrc;
   key.alpha = b.alpha;
   key.spread_width = b.spread_width;
+  key.spread_hot = b.spread_hot;
   key.max_rounds = b.max_rounds;
   key.balance = b.balance;
   key.bal[0] = b.bal_scale;
@@ -443,6 +444,7 @@ int fora::run_batch_ws(fora_graph* g, Workspace* w, const fora_params* p,
   {
     std::lock_guard<std::mutex> tlock(g->mu);
     b.spread_width = g->tune.spread_width;
+    b.spread_hot = (g->tune.spread_hot != 0 && g->nhot > 0) ? 1 : 0;
     b.walk_blocks = g->tune.walk_blocks;
     b.max_rounds = g->tune.max_push_rounds;
     host_loop = g->tune.push_host_loop != 0;
@@ -763,6 +765,37 @@ int fora_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col, uin
     if (e == cudaSuccess)
       e = cudaMemcpy(g->rd, rd.data(), (size_t)n * sizeof(uint2), cudaMemcpyHostToDevice);
   }
+  if (e == cudaSuccess) {
+    // hot targets of the spread: the kHotSlots nodes of highest in-degree (ties at the
+    // cut leave all tied nodes out), each with in-degree >= kHotMinIndeg
+    std::vector<uint32_t> indeg((size_t)n, 0u);
+    for (int64_t k = 0; k < m; ++k) ++indeg[(size_t)col[k]];
+    std::vector<uint32_t> sorted(indeg);
+    uint32_t cut = kHotMinIndeg;  // hot: in-degree >= cut
+    if ((int64_t)sorted.size() > kHotSlots) {
+      std::nth_element(sorted.begin(), sorted.end() - (kHotSlots + 1), sorted.end());
+      cut = std::max(cut, sorted[sorted.size() - (kHotSlots + 1)] + 1u);
+    }
+    std::vector<uint32_t> hot, code((size_t)n);
+    for (int64_t v = 0; v < n; ++v) {
+      code[v] = (uint32_t)v;
+      if (indeg[v] >= cut) {
+        code[v] = kHotBit | (uint32_t)hot.size();
+        hot.push_back((uint32_t)v);
+      }
+    }
+    if (!hot.empty()) {
+      std::vector<uint32_t> sc((size_t)m);
+      for (int64_t k = 0; k < m; ++k) sc[k] = code[(size_t)col[k]];
+      e = dalloc(&g->scol, (size_t)m * sizeof(uint32_t));
+      if (e == cudaSuccess) e = dalloc(&g->hot_node, hot.size() * sizeof(uint32_t));
+      if (e == cudaSuccess)
+        e = cudaMemcpy(g->scol, sc.data(), (size_t)m * sizeof(uint32_t), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(g->hot_node, hot.data(), hot.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) g->nhot = (int)hot.size();
+    }
+  }
   if (e == cudaSuccess) e = dalloc(&g->indeg, (size_t)n * sizeof(uint32_t));
   if (e == cudaSuccess) {
     const GraphDev gd = g->dev();
@@ -793,6 +826,8 @@ void fora_graph_destroy(fora_graph* g) {
     dfree(g->indeg);
     dfree(g->invd);
     dfree(g->rd);
+    dfree(g->scol);
+    dfree(g->hot_node);
     dfree(g->idx_off);
     dfree(g->idx_dest);
   }
@@ -1091,6 +1126,11 @@ int fora_graph_tune(fora_graph* g, const char* key, int64_t value) {
   if (strcmp(key, "spread_width") == 0) {
     if (value < 1 || value > 4096) return fail(FORA_ERR_BAD_ARG, "spread_width must be in [1, 4096]");
     g->tune.spread_width = (int)value;
+    return FORA_OK;
+  }
+  if (strcmp(key, "spread_hot") == 0) {
+    if (value != 0 && value != 1) return fail(FORA_ERR_BAD_ARG, "spread_hot must be 0 or 1");
+    g->tune.spread_hot = (int)value;
     return FORA_OK;
   }
   if (strcmp(key, "walk_blocks") == 0) {
@@ -1467,6 +1507,8 @@ int fora_graph_tuning(fora_graph* g, const char* key, int64_t* value) {
   if (!g || !key || !value) return fail(FORA_ERR_BAD_ARG, "null graph, key or value");
   std::lock_guard<std::mutex> lock(g->mu);
   if (strcmp(key, "spread_width") == 0) { *value = g->tune.spread_width; return FORA_OK; }
+  if (strcmp(key, "spread_hot") == 0) { *value = g->tune.spread_hot; return FORA_OK; }
+  if (strcmp(key, "hot_nodes") == 0) { *value = g->nhot; return FORA_OK; }
   if (strcmp(key, "walk_blocks") == 0) { *value = g->tune.walk_blocks; return FORA_OK; }
   if (strcmp(key, "pipeline") == 0) { *value = g->tune.pipeline; return FORA_OK; }
   if (strcmp(key, "push_host_loop") == 0) { *value = g->tune.push_host_loop; return FORA_OK; }

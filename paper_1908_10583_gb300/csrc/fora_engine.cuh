@@ -69,7 +69,25 @@ struct GraphDev {
   int colbits;
   const double* invd;   // [n] RN(1 / d(v)): the push increment is a product, not a quotient
   const uint2* rd;      // [n] {row[v], d(v)}: a walk's move reads one aligned 8-byte record
+  // The spread's copy of the targets (null when the graph has no hot nodes): the target
+  // id, or kHotBit | h for the h-th hot node (a node of high in-degree, hot_node[h]), whose
+  // increments a block sums in shared memory before one reduction reaches L2.
+  const uint32_t* scol;
+  const uint32_t* hot_node;  // [nhot] ascending ids
+  int nhot;
 };
+
+// Hot targets of the spread: at most kHotSlots nodes, each of in-degree >= kHotMinIndeg.
+// (2^20 R-MAT graph, 256 sources, push of the rule's / half the rule's r_max: 2048 hot
+// nodes 100.5 / 151.8 ms, 1024: 98.6 / 146.6, 256: 97.1 / 140.5, 128: 97.3 / 138.1,
+// 16: 98.7 / 138.6, one atomic per push 116.9 / 168.6; what the sums remove is mostly
+// the queueing of reductions on the same few addresses at L2.)
+#ifndef FORA_HOT_SLOTS
+#define FORA_HOT_SLOTS 128
+#endif
+constexpr int kHotSlots = FORA_HOT_SLOTS;
+constexpr uint32_t kHotMinIndeg = 64;
+constexpr uint32_t kHotBit = 0x80000000u;
 
 // Target e of a bit-packed column array (two 32-bit words always readable).
 __device__ __forceinline__ uint32_t packed_target(const uint32_t* colp, int bits, uint32_t e) {
@@ -153,6 +171,7 @@ struct BatchDev {
   unsigned long long* totals;     // [2]: |R|, W
   int residual_grid;
   int spread_width;  // interleaved segments of the frontier the spread visits at once
+  int spread_hot;    // the spread sums hot targets per block (GraphDev::scol is set)
   int walk_blocks;   // resident walk blocks per SM (3, 4 or 5)
   uint32_t max_rounds;  // push rounds allowed before kErrPushNotConverged
   // Balanced push (Section 4.2, Alg. 3): balance != 0 makes rmax the per-source threshold
@@ -178,6 +197,7 @@ struct BatchDev {
 // Launch-shape parameters of a graph (set through fora_graph_tune or the autotuner).
 struct Tuning {
   int spread_width = 1;
+  int spread_hot = 1;      // 1: heavy spread rounds sum hot targets' increments per block
   int walk_blocks = 4;
   int push_host_loop = 0;  // 1: rounds launched from a host loop instead of the graph
   int pipeline = 1;        // parts of a batch run on their own streams, pushes staggered

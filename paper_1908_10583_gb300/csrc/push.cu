@@ -162,15 +162,15 @@ __constant__ double kMultiple[33] = {0,  1,  2,  3,  4,  5,  6,  7,  8,  9,  10,
                                      11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21,
                                      22, 23, 24, 25, 26, 27, 28, 29, 30, 31, 32};
 
-// r[base + u] += inc for the active lanes of one 32-edge slice whose lanes hold consecutive
-// CSR entries (lane order = entry order; inactive lanes only at the end).  Rows are
-// sorted, so the copies of a multi-edge (v, u) are adjacent: a run of lanes with the same
-// target from the same frontier node (`owner`) becomes one reduction of k * inc by its
-// first lane (k copies counted with multiplicity, as Alg. 1 pushes along each of them;
-// one rounding instead of k, which only reorders the FP64 sum like the atomics do).
-__device__ __forceinline__ void spread_slice(double* r, unsigned long long base, uint32_t u,
-                                             uint32_t owner, double inc, bool act,
-                                             uint32_t* err, unsigned long long n) {
+// Runs of one 32-edge slice whose lanes hold consecutive CSR entries (lane order = entry
+// order; inactive lanes only at the end).  Rows are sorted, so the copies of a multi-edge
+// (v, u) are adjacent: a run of lanes with the same target from the same frontier node
+// (`owner`) becomes one add of k * inc by its first lane (k copies counted with
+// multiplicity, as Alg. 1 pushes along each of them; one rounding instead of k, which only
+// reorders the FP64 sum like the atomics do).  True for the first lane of a run, with
+// add = k * inc; every lane of the warp calls it.
+__device__ __forceinline__ bool run_lead(uint32_t u, uint32_t owner, double inc, bool act,
+                                         double& add) {
   const uint32_t lane = lane_id();
   const uint32_t pu = __shfl_up_sync(kFull, u, 1);
   const uint32_t po = __shfl_up_sync(kFull, owner, 1);
@@ -184,11 +184,19 @@ __device__ __forceinline__ void spread_slice(double* r, unsigned long long base,
   }
   // FP64 arithmetic only in slices that hold a run (this GPU's FP64 rate is low, and most
   // slices have none); kMultiple[k] = k avoids an integer-to-FP64 conversion
-  double add = inc;
+  add = inc;
   if (__any_sync(kFull, k > 1u)) {
     if (k > 1u) add = __dmul_rn(inc, kMultiple[k]);
   }
-  if (lead && FORA_IN_RANGE(err, u, n)) atomicAdd(&r[base + u], add);
+  return lead;
+}
+
+// r[base + u] += inc for the active lanes of one slice, one reduction per run.
+__device__ __forceinline__ void spread_slice(double* r, unsigned long long base, uint32_t u,
+                                             uint32_t owner, double inc, bool act,
+                                             uint32_t* err, unsigned long long n) {
+  double add;
+  if (run_lead(u, owner, inc, act, add) && FORA_IN_RANGE(err, u, n)) atomicAdd(&r[base + u], add);
 }
 
 // Work is handed out dynamically (kGrab groups or hub items per atomic), so the warps
@@ -327,6 +335,257 @@ __global__ void __launch_bounds__(kSpreadThreads, FORA_SPREAD_MIN_BLOCKS) k_push
         for (int k = 0; k < (int)(kHubChunk / 32); ++k)
           if (u[k] < n) dirty[u[k] / kTileNodes] = 1;
       }
+    }
+  }
+}
+
+// The spread with hot targets summed per block (GraphDev::scol set, BatchDev::spread_hot).
+// In the R-MAT graphs a few thousand nodes of high in-degree receive a large share of all
+// edge pushes, and every push is an FP64 reduction at L2, the spread's bound.  Here a
+// block takes kHotRange consecutive groups (or hub items) of one interleaved segment of
+// the frontier at a time.  Where the range holds at least kHotStretch items of one source
+// in a heavy round (the source's round is not light), the block processes that stretch
+// together: its adds to hot nodes go to a shared-memory array, and after the stretch one
+// reduction per touched hot node carries each sum to r.  The rest of the range (light
+// rounds, whose spread also marks the tiles it touches, and short stretches) is spread
+// first, warp by warp, with one reduction per push as in k_push_spread.  Summing in
+// shared memory first only regroups the FP64 sum, as the order of the atomics does.
+// Range and stretch measured on the 2^20 R-MAT graph (2048 hot nodes, 5 blocks per SM):
+// ranges of 16, 24, 32, 64, 128 items gave 103.4, 101.2, 100.5, 110.7, 141.3 ms of push
+// with the rule's r_max (fewer, larger ranges leave blocks idle at the end of a round);
+// a minimum stretch of 4, 8 or 16 items made no difference.
+#ifndef FORA_HOT_RANGE
+#define FORA_HOT_RANGE 32
+#endif
+constexpr unsigned long long kHotRange = FORA_HOT_RANGE;
+#ifndef FORA_HOT_STRETCH
+#define FORA_HOT_STRETCH 8
+#endif
+constexpr unsigned long long kHotStretch = FORA_HOT_STRETCH;
+
+// Node id of a target code of GraphDev::scol.
+__device__ __forceinline__ uint32_t hot_decode(const GraphDev& g, uint32_t code) {
+  return (code & kHotBit) ? g.hot_node[code & ~kHotBit] : code;
+}
+
+__device__ __forceinline__ void hot_slice(const GraphDev& g, double* r, unsigned long long base,
+                                          double* hacc, bool agg, uint32_t code, uint32_t owner,
+                                          double inc, bool act, uint32_t* err,
+                                          unsigned long long n) {
+  double add;
+  if (!run_lead(code, owner, inc, act, add)) return;
+  if (code & kHotBit) {
+    const uint32_t h = code & ~kHotBit;
+    if (!FORA_IN_RANGE(err, h, (uint32_t)g.nhot)) return;
+    if (agg) atomicAdd(&hacc[h], add);
+    else atomicAdd(&r[base + g.hot_node[h]], add);
+  } else if (FORA_IN_RANGE(err, code, n)) {
+    atomicAdd(&r[base + code], add);
+  }
+}
+
+// Light rounds: the tiles of the targets of up to 32 pushes (act) are marked.
+__device__ __forceinline__ void hot_mark(const GraphDev& g, const BatchDev& b, int cs,
+                                         uint32_t code, bool act) {
+  const unsigned long long n = (unsigned long long)g.n;
+  if (!act) return;
+  const uint32_t x = hot_decode(g, code);
+  if (x < n) b.tile_dirty[(unsigned long long)cs * b.tiles + x / kTileNodes] = 1;
+}
+
+// Group grp of source cs (its groups start at clo, its frontier has ccnt entries): the
+// out-edges of 32 frontier entries with d <= kHubChunk, 128 edges per iteration.
+__device__ __forceinline__ void hot_group(const GraphDev& g, const BatchDev& b,
+                                          const unsigned long long* q, int cs,
+                                          unsigned long long clo, uint32_t ccnt,
+                                          unsigned long long grp, bool light, bool agg,
+                                          double* hacc) {
+  const uint32_t lane = lane_id();
+  const unsigned long long n = (unsigned long long)g.n;
+  const unsigned long long base_gi = (unsigned long long)cs * n;
+  const uint32_t i = (uint32_t)(grp - clo) * 32u + lane;
+  uint32_t c = 0, rb = 0;
+  double inc = 0.0;
+  if (i < ccnt) {
+    const uint32_t v = (uint32_t)q[base_gi + i];
+    rb = g.row[v];
+    const uint32_t d = g.row[v + 1] - rb;
+    if (d <= kHubChunk) {
+      c = d;
+      inc = b.fa[base_gi + i];
+    }
+  }
+  const uint32_t incl = warp_incl_scan(c);
+  const uint32_t total = __shfl_sync(kFull, incl, 31);
+  const uint32_t excl = incl - c;
+  for (uint32_t base = 0; base < total; base += 128) {
+    uint32_t u[4], own[4];
+    double ik[4];
+    bool act[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t e = base + 32 * k + lane;
+      int lo = 0, hi = 31;  // owner: the first lane whose inclusive prefix exceeds e
+#pragma unroll
+      for (int s2 = 0; s2 < 5; ++s2) {
+        const int mid = (lo + hi) >> 1;
+        if (__shfl_sync(kFull, incl, mid) > e) hi = mid; else lo = mid + 1;
+      }
+      const uint32_t ek = __shfl_sync(kFull, excl, lo);
+      const uint32_t rbk = __shfl_sync(kFull, rb, lo);
+      ik[k] = __shfl_sync(kFull, inc, lo);
+      own[k] = (uint32_t)lo;
+      act[k] = e < total;
+      u[k] = act[k] ? g.scol[rbk + (e - ek)] : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      hot_slice(g, b.r, base_gi, hacc, agg, u[k], own[k], ik[k], act[k], b.err, n);
+    if (light) {  // warp-uniform
+#pragma unroll
+      for (int k = 0; k < 4; ++k) hot_mark(g, b, cs, u[k], act[k]);
+    }
+  }
+}
+
+// Hub item h of source cs (its items start at clo): kHubChunk out-edges of one node.
+__device__ __forceinline__ void hot_hub(const GraphDev& g, const BatchDev& b,
+                                        const unsigned long long* q, int cur, int cs,
+                                        unsigned long long clo, unsigned long long h, bool light,
+                                        bool agg, double* hacc) {
+  const uint32_t lane = lane_id();
+  const unsigned long long n = (unsigned long long)g.n;
+  const unsigned long long item = b.hub[cur][(unsigned long long)cs * b.hub_stride + (h - clo)];
+  const unsigned long long fi = item >> kHubChunkBits;
+  const uint32_t c = (uint32_t)(item & ((1ull << kHubChunkBits) - 1));
+  const uint32_t v = (uint32_t)q[fi];
+  const uint32_t rb = g.row[v], re = g.row[v + 1];
+  const double inc = b.fa[fi];
+  const uint32_t beg = rb + c * kHubChunk;
+  const uint32_t end = min(beg + kHubChunk, re);
+  uint32_t u[kHubChunk / 32];
+  bool act[kHubChunk / 32];
+#pragma unroll
+  for (int k = 0; k < (int)(kHubChunk / 32); ++k) {
+    const uint32_t p = beg + 32 * k + lane;
+    act[k] = p < end;
+    u[k] = act[k] ? g.scol[p] : 0u;
+  }
+#pragma unroll
+  for (int k = 0; k < (int)(kHubChunk / 32); ++k)
+    hot_slice(g, b.r, (unsigned long long)cs * n, hacc, agg, u[k], 0u, inc, act[k], b.err, n);
+  if (light) {  // warp-uniform
+#pragma unroll
+    for (int k = 0; k < (int)(kHubChunk / 32); ++k) hot_mark(g, b, cs, u[k], act[k]);
+  }
+}
+
+// Item x of a phase (0: groups, 1: hub items) of source cs.
+__device__ __forceinline__ void hot_item(const GraphDev& g, const BatchDev& b, int phase,
+                                         const unsigned long long* q, int cur,
+                                         const uint32_t* cnt, int cs, unsigned long long clo,
+                                         unsigned long long x, bool light, bool agg,
+                                         double* hacc) {
+  if (phase == 0)
+    hot_group(g, b, q, cs, clo, cnt[cs], x, light, agg, hacc);
+  else
+    hot_hub(g, b, q, cur, cs, clo, x, light, agg, hacc);
+}
+
+// The items of source cs in the range [lo, hi) are summed in shared memory when the
+// source's round is heavy and they are at least kHotStretch.
+__device__ __forceinline__ bool hot_summed(const BatchDev& b, const unsigned long long* pre,
+                                           int cs, unsigned long long lo, unsigned long long hi) {
+  const unsigned long long s0 = max(lo, pre[cs]), s1 = min(hi, pre[cs + 1]);
+  return b.light[cs] == 0 && s1 - s0 >= kHotStretch;
+}
+
+// 5 resident blocks (48 registers): 6 (40 registers, a few spilled) and 4 were slower by
+// 2-4% and 3-10%.
+#ifndef FORA_SPREAD_HOT_MIN_BLOCKS
+#define FORA_SPREAD_HOT_MIN_BLOCKS 5
+#endif
+__global__ void __launch_bounds__(kSpreadThreads, FORA_SPREAD_HOT_MIN_BLOCKS)
+    k_push_spread_hot(GraphDev g, BatchDev b) {
+  __shared__ double hacc[kHotSlots];
+  __shared__ unsigned long long s_range[2];  // one per phase: no thread reads a stale one
+  __shared__ uint32_t s_next;
+  const int cur = b.ps->cur;
+  const unsigned long long* q = b.q[cur];
+  const uint32_t* cnt = b.slot_cnt + (size_t)cur * b.cnt_stride;
+  const unsigned long long width = (unsigned long long)b.spread_width;
+  const uint32_t lane = lane_id();
+  const unsigned long long base_n = (unsigned long long)g.n;
+  for (int h = threadIdx.x; h < g.nhot; h += blockDim.x) hacc[h] = 0.0;
+
+  // phase 0: groups, phase 1: hub items; segment k of a phase's items is
+  // [k * seg, min((k + 1) * seg, total)), taken kHotRange items at a time, the ranges of
+  // the segments interleaved
+  for (int phase = 0; phase < 2; ++phase) {
+    const unsigned long long total = phase == 0 ? b.ps->ngroups : b.ps->nhub;
+    const unsigned long long* pre = phase == 0 ? b.gpre : b.hpre;
+    unsigned long long* work = b.work + (phase == 0 ? 0 : 16);
+    const unsigned long long seg = (total + width - 1) / width;
+    const unsigned long long rseg = (seg + kHotRange - 1) / kHotRange;
+    const unsigned long long rtotal = rseg * width;
+    for (;;) {
+      if (threadIdx.x == 0) {
+        s_range[phase] = atomicAdd(work, 1ull);
+        s_next = 0;
+      }
+      __syncthreads();
+      const unsigned long long vr = s_range[phase];
+      if (vr >= rtotal) break;  // block-uniform
+      const unsigned long long sbeg = (vr % width) * seg;
+      const unsigned long long lo = sbeg + (vr / width) * kHotRange;
+      const unsigned long long hi = min(lo + kHotRange, min(sbeg + seg, total));
+      // the items not summed, warp by warp with one reduction per push
+      int cs = 0;
+      unsigned long long clo = 1, chi = 0;
+      bool skip = false, light = false;
+      for (;;) {
+        uint32_t k = 0;
+        if (lane == 0) k = atomicAdd(&s_next, 1u);
+        k = __shfl_sync(kFull, k, 0);
+        const unsigned long long x = lo + k;
+        if (x >= hi) break;  // warp-uniform
+        if (x < clo || x >= chi) {  // warp-uniform
+          cs = slot_of(pre, b.nsrc, x);
+          clo = pre[cs];
+          chi = pre[cs + 1];
+          skip = hot_summed(b, pre, cs, lo, hi);
+          light = b.light[cs] != 0;
+        }
+        if (!skip) hot_item(g, b, phase, q, cur, cnt, cs, clo, x, light, false, hacc);
+      }
+      // the summed stretches, one source at a time with the whole block
+      for (unsigned long long x = lo; x < hi;) {  // block-uniform
+        const int s = slot_of(pre, b.nsrc, x);
+        const unsigned long long s1 = min(hi, pre[s + 1]);
+        if (hot_summed(b, pre, s, lo, hi)) {
+          __syncthreads();  // s_next free, hacc zero
+          if (threadIdx.x == 0) s_next = 0;
+          __syncthreads();
+          for (;;) {
+            uint32_t k = 0;
+            if (lane == 0) k = atomicAdd(&s_next, 1u);
+            k = __shfl_sync(kFull, k, 0);
+            if (x + k >= s1) break;  // warp-uniform
+            hot_item(g, b, phase, q, cur, cnt, s, pre[s], x + k, false, true, hacc);
+          }
+          __syncthreads();  // every add of the stretch is in hacc
+          const unsigned long long base = (unsigned long long)s * base_n;
+          for (int h = threadIdx.x; h < g.nhot; h += blockDim.x) {
+            const double a = hacc[h];
+            if (a != 0.0) {  // every add is positive: zero means untouched
+              atomicAdd(&b.r[base + g.hot_node[h]], a);
+              hacc[h] = 0.0;
+            }
+          }
+        }
+        x = s1;
+      }
+      __syncthreads();  // s_range, s_next and hacc free for the next range
     }
   }
 }
@@ -643,10 +902,15 @@ cudaError_t launch_push_body(const GraphDev& g, const BatchDev& b, int num_sms,
                              cudaGraphConditionalHandle loop, bool in_graph, cudaStream_t st) {
   // one wave of resident blocks for the spread (with the dynamic work counter the warps
   // in flight cover one contiguous window of the frontier) and for the take
-  const int spread_per_sm = resident_blocks((const void*)k_push_spread, kSpreadThreads);
+  const bool hot = b.spread_hot && g.scol && g.nhot > 0;
+  const void* spread = hot ? (const void*)k_push_spread_hot : (const void*)k_push_spread;
+  const int spread_per_sm = resident_blocks(spread, kSpreadThreads);
   const int take_per_sm = resident_blocks((const void*)k_push_take, kTakeThreads);
   if (spread_per_sm == 0 || take_per_sm == 0) return cudaErrorInvalidConfiguration;
-  k_push_spread<<<num_sms * spread_per_sm, kSpreadThreads, 0, st>>>(g, b);
+  if (hot)
+    k_push_spread_hot<<<num_sms * spread_per_sm, kSpreadThreads, 0, st>>>(g, b);
+  else
+    k_push_spread<<<num_sms * spread_per_sm, kSpreadThreads, 0, st>>>(g, b);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_push_take<<<num_sms * take_per_sm, kTakeThreads, 0, st>>>(g, b);

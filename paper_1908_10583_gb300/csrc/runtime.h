@@ -41,12 +41,14 @@ struct PushGraphKey {
   int nsrc = 0;
   double alpha = 0.0;
   int spread_width = 0;
+  int spread_hot = 0;
   uint32_t max_rounds = 0;
   int balance = 0;
   double bal[4] = {0, 0, 0, 0};  // C', cost_edge, cost_push, cost_walk (balanced push)
   bool operator==(const PushGraphKey& o) const {
     return generation == o.generation && nsrc == o.nsrc && alpha == o.alpha &&
-           spread_width == o.spread_width && max_rounds == o.max_rounds &&
+           spread_width == o.spread_width && spread_hot == o.spread_hot &&
+           max_rounds == o.max_rounds &&
            balance == o.balance && bal[0] == o.bal[0] && bal[1] == o.bal[1] &&
            bal[2] == o.bal[2] && bal[3] == o.bal[3];
   }
@@ -187,6 +189,9 @@ struct fora_graph {
   uint32_t* indeg = nullptr;  // in-degrees (features of the learned r_max)
   double* invd = nullptr;     // RN(1 / d(v)) per node
   uint2* rd = nullptr;        // {row[v], d(v)} per node (the walks' node record)
+  uint32_t* scol = nullptr;   // the spread's target codes (GraphDev::scol), or null
+  uint32_t* hot_node = nullptr;
+  int nhot = 0;
   // FORA+ walk index (Section 3.3): ends of omega_max(v) walks from every v
   unsigned long long* idx_off = nullptr;  // [n + 1] exclusive prefix of omega_max
   uint32_t* idx_dest = nullptr;           // [idx_entries] walk ends
@@ -202,7 +207,9 @@ struct fora_graph {
   // parts of a pipelined batch: a workspace and a stream each
   fora::Workspace pipe_ws[fora::kMaxPipeline];
   cudaStream_t pipe_stream[fora::kMaxPipeline] = {};
-  fora::GraphDev dev() const { return fora::GraphDev{n, m, row, col, colp, colbits, invd, rd}; }
+  fora::GraphDev dev() const {
+    return fora::GraphDev{n, m, row, col, colp, colbits, invd, rd, scol, hot_node, nhot};
+  }
 };
 
 namespace fora {

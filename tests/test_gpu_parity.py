@@ -79,12 +79,31 @@ def test_resolved_parameters_are_bit_identical_to_the_oracle(rmat14):
         assert t == oracle.alpha_threshold(0.2)
 
 
-def test_push_matches_oracle(rmat14):
+def hot_count(col, n):
+    """Hot nodes of the push (the up to 128 of highest in-degree, each >= 64, ties at the
+    cut left out), counted from the in-degrees."""
+    indeg = np.bincount(np.asarray(col, dtype=np.int64), minlength=n)
+    cut = 64
+    if n > 128:
+        cut = max(cut, int(np.sort(indeg)[n - 129]) + 1)
+    return int((indeg >= cut).sum())
+
+
+@pytest.mark.parametrize("spread_hot", [1, 0])
+def test_push_matches_oracle(rmat14, spread_hot):
+    """Push reserves and residues against the oracle, with the hot-node sums of the
+    spread (1, the default) and with one atomic per push (0)."""
     rp, col, g = rmat14
     n = len(rp) - 1
+    nhot = g.tuning("hot_nodes")
+    assert nhot == hot_count(col, n) and 0 < nhot <= 128
     sources = inputs.uniform_sources(n, 10, inputs.SOURCE_SEED)
     p = fora.Params.make(k=50)
-    ids, vals, st, out = run_debug(g, sources, p)
+    g.tune("spread_hot", spread_hot)
+    try:
+        ids, vals, st, out = run_debug(g, sources, p)
+    finally:
+        g.tune("spread_hot", 1)
     rmax = g.resolve(p)[0]
     for i, s in enumerate(sources):
         res, r, pst = oracle.forward_push(rp, col, s, 0.2, rmax)
@@ -342,8 +361,13 @@ def test_host_driven_push_loop_matches_oracle(rmat14):
     g.tune("push_host_loop", 1)
     try:
         _, _, st, out = run_debug(g, sources, p)
+        g.tune("spread_hot", 0)
+        _, _, st0, out0 = run_debug(g, sources, p)
     finally:
         g.tune("push_host_loop", 0)
+        g.tune("spread_hot", 1)
+    np.testing.assert_allclose(out0["reserve"], out["reserve"], rtol=0, atol=ATOL_PUSH)
+    assert [x.pushes for x in st0] == [x.pushes for x in st]
     for i, s in enumerate(sources):
         res_o, r_o, pst = oracle.forward_push(rp, col, int(s), 0.2, rmax)
         np.testing.assert_allclose(out["reserve"][i], res_o, rtol=0, atol=ATOL_PUSH)
@@ -351,6 +375,8 @@ def test_host_driven_push_loop_matches_oracle(rmat14):
         assert st[i].pushes == pst.pushes and st[i].push_rounds == pst.rounds
     with pytest.raises(fora.FORAError):
         g.tune("push_host_loop", 2)
+    with pytest.raises(fora.FORAError):
+        g.tune("spread_hot", 2)
 
 
 def test_device_frontier_test_equals_fp64_comparison():

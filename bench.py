@@ -512,7 +512,9 @@ def run_fora(args):
         roofline["issue_l2_source"] = "ncu section capture, profiles/k_walks_" + args.workload + ".txt"
     # the push phase (all its rounds: spread, take, advance) against the same peak
     achieved_push = (sum(push_bytes) / len(push_bytes)) / (statistics.mean(push_ms) / 1e3) / 1e9
-    roofline_push = {"bound": "hbm", "kernels": "k_push_spread+k_push_take+k_push_advance",
+    spread_kernel = ("k_push_spread_hot" if tuning.get("spread_hot") and tuning.get("hot_nodes")
+                     else "k_push_spread")
+    roofline_push = {"bound": "hbm", "kernels": spread_kernel + "+k_push_take+k_push_advance",
                      "achieved": achieved_push, "peak": peak, "peak_kind": peak_kind,
                      "unit": "GB/s", "frac": achieved_push / peak,
                      "traffic": profiled_traffic("push", args.workload, 1, "dram_bytes_per_step"),

@@ -450,10 +450,11 @@ int fora_graph_tuning(fora_graph *g, const char *key, int64_t *value);
 /*
  * Autotuner over the launch shapes of fora_graph_tune: runs the batched query on the
  * given sources (HOST array, a representative batch) once to warm up, then with
- * spread_width 1, 2, 4, 8, 16 keeping the fastest push phase, then with walk_blocks
- * 3, 4, 5 ("walk_blocks": resident 256-thread walk blocks per SM, i.e. the register
- * budget of the walk kernel) keeping the fastest walk phase (both with "pipeline" 1),
- * then, for nsrc >= 64, "pipeline" 1 or 2 by the whole batch's time (the faster of two
+ * spread_width 1, 2, 4, 8, 16 keeping the fastest push phase, then (when the graph
+ * has hot nodes) with "spread_hot" 0 and 1 at that width keeping the faster push, then
+ * with walk_blocks 3, 4, 5 ("walk_blocks": resident 256-thread walk blocks per SM, i.e.
+ * the register budget of the walk kernel) keeping the fastest walk phase (all with
+ * "pipeline" 1), then, for nsrc >= 64, "pipeline" 1 or 2 by the whole batch's time (the faster of two
  * runs each).  The choices stay set on the graph; spread_width and walk_blocks are
  * returned (either pointer may be NULL), all of them through fora_graph_tuning.
  * Results of queries do not depend on them.

@@ -288,14 +288,14 @@ class Graph:
 
     def autotune(self, sources, params: Params, stream=None):
         """fora_graph_autotune on a representative batch -> {spread_width, walk_blocks,
-        pipeline}."""
+        pipeline, spread_hot}."""
         src = np.ascontiguousarray(sources, dtype=np.int32)
         sw, wb = ctypes.c_int32(), ctypes.c_int32()
         _check(load().fora_graph_autotune(self._h, ctypes.byref(params), src.ctypes.data,
                                           len(src), ctypes.byref(sw), ctypes.byref(wb),
                                           _stream_ptr(stream)))
         return {"spread_width": sw.value, "walk_blocks": wb.value,
-                "pipeline": self.tuning("pipeline")}
+                "pipeline": self.tuning("pipeline"), "spread_hot": self.tuning("spread_hot")}
 
     def info(self):
         n, m, d = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()

@@ -1453,6 +1453,21 @@ int fora_graph_autotune(fora_graph* g, const fora_params* params, const int32_t*
     std::lock_guard<std::mutex> lock(g->mu);
     g->tune.spread_width = best_sw;
   }
+  // the hot-node sums of the spread against one reduction per push, at that width
+  if (g->nhot > 0) {
+    float hot_ms[2] = {0, 0};
+    for (int h = 0; h <= 1; ++h) {
+      {
+        std::lock_guard<std::mutex> lock(g->mu);
+        g->tune.spread_hot = h;
+      }
+      rc = run(&pm, &wm);
+      if (rc) return rc;
+      hot_ms[h] = pm;
+    }
+    std::lock_guard<std::mutex> lock(g->mu);
+    g->tune.spread_hot = hot_ms[1] <= hot_ms[0] ? 1 : 0;
+  }
   for (int wb = 3; wb <= 5; ++wb) {
     {
       std::lock_guard<std::mutex> lock(g->mu);

@@ -334,6 +334,7 @@ def test_autotuner_and_launch_shapes_do_not_change_results(rmat14):
     choice = g.autotune(sources, p)
     assert choice["spread_width"] in (1, 2, 4, 8, 16) and choice["walk_blocks"] in (3, 4, 5)
     assert choice["pipeline"] == 1  # 12 sources: too few to split
+    assert choice["spread_hot"] in (0, 1) and g.tuning("spread_hot") == choice["spread_hot"]
     assert g.tuning("walk_blocks") == choice["walk_blocks"]
     for sw, wb in [(1, 3), (16, 5), (3, 4), (choice["spread_width"], choice["walk_blocks"])]:
         g.tune("spread_width", sw)
@@ -348,6 +349,7 @@ def test_autotuner_and_launch_shapes_do_not_change_results(rmat14):
         g.tune("walk_blocks", 6)
     g.tune("spread_width", 1)
     g.tune("walk_blocks", 4)
+    g.tune("spread_hot", 1)
 
 
 def test_host_driven_push_loop_matches_oracle(rmat14):

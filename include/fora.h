@@ -142,6 +142,18 @@ typedef struct {
 int fora_graph_create(int64_t n, const int64_t *row_ptr, const int32_t *col, uint32_t flags,
                       fora_graph **out);
 
+/*
+ * The hot nodes of a CSR graph, as fora_graph_create marks them for the push (host
+ * arithmetic only, no device): the up to 128 nodes of highest in-degree, each of
+ * in-degree >= 64, where nodes tied at the cut are all left out; ascending ids.
+ * row_ptr (n+1 entries, row_ptr[0] = 0) and col (row_ptr[n] ids in [0, n)) are HOST
+ * arrays, read only.  Writes the first min(count, capacity) ids to out (capacity may be
+ * 0, out then may be NULL) and the number of hot nodes to *count.  Errors:
+ * FORA_ERR_BAD_ARG for bad sizes, null pointers or an id out of range.
+ */
+int fora_hot_nodes(int64_t n, const int64_t *row_ptr, const int32_t *col, int32_t *out,
+                   int32_t capacity, int32_t *count);
+
 /* Release the graph and its workspace.  NULL is accepted. */
 void fora_graph_destroy(fora_graph *g);
 

@@ -9,12 +9,12 @@ from ._native import (Balance, DebugIO, FORAError, Graph, Model, Params, Server,
                       FORA_ERR_BAD_ARG, FORA_ERR_CUDA, FORA_ERR_DANGLING, FORA_ERR_OOM,
                       FORA_ERR_PUSH_NOT_CONVERGED, FORA_ERR_TIMEOUT, FORA_ERR_WALK_CAP,
                       FORA_ERR_WALK_OVERFLOW, FORA_MAX_K, FORA_OK, FORA_OUT_DEVICE, FORA_USE_INDEX,
-                      FORA_ZERO_HOP, debug_fail_alloc, header_functions, lib_path, load, philox,
-                      threshold, topk, workspace_bytes)
+                      FORA_ZERO_HOP, debug_fail_alloc, header_functions, hot_nodes, lib_path,
+                      load, philox, threshold, topk, workspace_bytes)
 
 __all__ = ["Balance", "DebugIO", "FORAError", "Graph", "Model", "Params", "Server", "Stats", "FORA_DBG_GIVEN_PUSH",
            "FORA_ERR_BAD_ARG", "FORA_ERR_CUDA", "FORA_ERR_DANGLING", "FORA_ERR_OOM",
            "FORA_ERR_PUSH_NOT_CONVERGED", "FORA_ERR_TIMEOUT", "FORA_ERR_WALK_CAP",
            "FORA_ERR_WALK_OVERFLOW", "FORA_MAX_K", "FORA_OK", "FORA_OUT_DEVICE", "FORA_USE_INDEX",
-           "FORA_ZERO_HOP", "debug_fail_alloc", "header_functions", "lib_path", "load", "philox",
-           "threshold", "topk", "workspace_bytes"]
+           "FORA_ZERO_HOP", "debug_fail_alloc", "header_functions", "hot_nodes", "lib_path", "load",
+           "philox", "threshold", "topk", "workspace_bytes"]

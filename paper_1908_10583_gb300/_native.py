@@ -188,6 +188,8 @@ def load():
         L.fora_index_destroy.argtypes = [P]
         L.fora_workspace_bytes.restype = I
         L.fora_workspace_bytes.argtypes = [i64, P, i32, P]
+        L.fora_hot_nodes.restype = I
+        L.fora_hot_nodes.argtypes = [i64, P, P, P, i32, P]
         L.fora_debug_checks.restype = I
         L.fora_debug_checks.argtypes = []
         L.fora_debug_fail_alloc.restype = I
@@ -481,6 +483,19 @@ def workspace_bytes(row_ptr, nsrc: int) -> int:
     out = ctypes.c_uint64()
     _check(load().fora_workspace_bytes(len(rp) - 1, rp.ctypes.data, int(nsrc), ctypes.byref(out)))
     return out.value
+
+
+def hot_nodes(row_ptr, col) -> np.ndarray:
+    """The hot nodes the push marks in this CSR graph (fora_hot_nodes, host arithmetic)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    c = np.ascontiguousarray(col, dtype=np.int32)
+    count = ctypes.c_int32()
+    _check(load().fora_hot_nodes(len(rp) - 1, rp.ctypes.data, c.ctypes.data, None, 0,
+                                 ctypes.byref(count)))
+    out = np.zeros(max(count.value, 1), dtype=np.int32)
+    _check(load().fora_hot_nodes(len(rp) - 1, rp.ctypes.data, c.ctypes.data, out.ctypes.data,
+                                 len(out), ctypes.byref(count)))
+    return out[:count.value]
 
 
 def debug_fail_alloc(nth: int):

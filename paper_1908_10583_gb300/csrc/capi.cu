@@ -671,6 +671,24 @@ int run_batch_pipelined(fora_graph* g, const fora_params* p, const int32_t* sour
   return FORA_OK;
 }
 
+// The hot nodes of the spread, ascending: the kHotSlots nodes of highest in-degree (ties
+// at the cut leave all tied nodes out), each with in-degree >= kHotMinIndeg.  col holds m
+// ids in [0, n).
+std::vector<uint32_t> hot_nodes_of(int64_t n, const int32_t* col, int64_t m) {
+  std::vector<uint32_t> indeg((size_t)n, 0u);
+  for (int64_t k = 0; k < m; ++k) ++indeg[(size_t)col[k]];
+  std::vector<uint32_t> sorted(indeg);
+  uint32_t cut = kHotMinIndeg;  // hot: in-degree >= cut
+  if ((int64_t)sorted.size() > kHotSlots) {
+    std::nth_element(sorted.begin(), sorted.end() - (kHotSlots + 1), sorted.end());
+    cut = std::max(cut, sorted[sorted.size() - (kHotSlots + 1)] + 1u);
+  }
+  std::vector<uint32_t> hot;
+  for (int64_t v = 0; v < n; ++v)
+    if (indeg[v] >= cut) hot.push_back((uint32_t)v);
+  return hot;
+}
+
 int run_batch(fora_graph* g, const fora_params* p, const int32_t* sources, int nsrc,
               int32_t* out_ids, double* out_vals, fora_stats* st, const fora_debug_io* dbg,
               uint32_t dbg_flags, cudaStream_t stream, RmaxSource rsrc = RmaxSource(),
@@ -766,24 +784,11 @@ int fora_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col, uin
       e = cudaMemcpy(g->rd, rd.data(), (size_t)n * sizeof(uint2), cudaMemcpyHostToDevice);
   }
   if (e == cudaSuccess) {
-    // hot targets of the spread: the kHotSlots nodes of highest in-degree (ties at the
-    // cut leave all tied nodes out), each with in-degree >= kHotMinIndeg
-    std::vector<uint32_t> indeg((size_t)n, 0u);
-    for (int64_t k = 0; k < m; ++k) ++indeg[(size_t)col[k]];
-    std::vector<uint32_t> sorted(indeg);
-    uint32_t cut = kHotMinIndeg;  // hot: in-degree >= cut
-    if ((int64_t)sorted.size() > kHotSlots) {
-      std::nth_element(sorted.begin(), sorted.end() - (kHotSlots + 1), sorted.end());
-      cut = std::max(cut, sorted[sorted.size() - (kHotSlots + 1)] + 1u);
-    }
-    std::vector<uint32_t> hot, code((size_t)n);
-    for (int64_t v = 0; v < n; ++v) {
-      code[v] = (uint32_t)v;
-      if (indeg[v] >= cut) {
-        code[v] = kHotBit | (uint32_t)hot.size();
-        hot.push_back((uint32_t)v);
-      }
-    }
+    // hot targets of the spread, and the target codes that mark them
+    const std::vector<uint32_t> hot = hot_nodes_of(n, col, m);
+    std::vector<uint32_t> code((size_t)n);
+    for (int64_t v = 0; v < n; ++v) code[v] = (uint32_t)v;
+    for (size_t h = 0; h < hot.size(); ++h) code[hot[h]] = kHotBit | (uint32_t)h;
     if (!hot.empty()) {
       std::vector<uint32_t> sc((size_t)m);
       for (int64_t k = 0; k < m; ++k) sc[k] = code[(size_t)col[k]];
@@ -806,6 +811,22 @@ int fora_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col, uin
     return bail(fail(e == cudaErrorMemoryAllocation ? FORA_ERR_OOM : FORA_ERR_CUDA, "graph upload: %s",
                      cudaGetErrorString(e)));
   *out = g;
+  return FORA_OK;
+}
+
+int fora_hot_nodes(int64_t n, const int64_t* row_ptr, const int32_t* col, int32_t* out,
+                   int32_t capacity, int32_t* count) {
+  if (n < 1 || n > 0x7FFFFFFF || !row_ptr || !col || capacity < 0 || (capacity > 0 && !out) ||
+      !count)
+    return fail(FORA_ERR_BAD_ARG, "bad arguments");
+  const int64_t m = row_ptr[n];
+  if (row_ptr[0] != 0 || m < 0 || m > 0xFFFFFFFFll)
+    return fail(FORA_ERR_BAD_ARG, "row_ptr must start at 0 and end below 2^32");
+  for (int64_t k = 0; k < m; ++k)
+    if (col[k] < 0 || col[k] >= n) return fail(FORA_ERR_BAD_ARG, "col[%lld] out of range", (long long)k);
+  const std::vector<uint32_t> hot = hot_nodes_of(n, col, m);
+  for (size_t h = 0; h < hot.size() && (int64_t)h < capacity; ++h) out[h] = (int32_t)hot[h];
+  *count = (int32_t)hot.size();
   return FORA_OK;
 }
 

@@ -113,3 +113,52 @@ def test_debug_build_has_index_checks_and_the_normal_build_not(lib):
     dbg = ctypes.CDLL(fbuild.build(debug=True))
     assert dbg.fora_debug_checks() == 1
     assert fora.header_functions() and all(hasattr(dbg, n) for n in fora.header_functions())
+
+
+def _hot_reference(col, n, slots=128, min_indeg=64):
+    """The hot-node rule written out with numpy: in-degree >= 64 and above the in-degree of
+    the (slots+1)-th largest, ascending ids."""
+    import numpy as np
+    indeg = np.bincount(np.asarray(col, dtype=np.int64), minlength=n)
+    cut = min_indeg
+    if n > slots:
+        cut = max(cut, int(np.sort(indeg)[n - slots - 1]) + 1)
+    return np.flatnonzero(indeg >= cut)
+
+
+def test_hot_nodes_of_the_push_follow_the_in_degree_rule(lib):
+    """The nodes the spread sums per block (host arithmetic, no device): the rule against a
+    numpy restatement on R-MAT graphs, a star, ties at the cut and graphs without hubs."""
+    import numpy as np
+    import inputs
+    for scale, deg, seed in [(14, 8, 1), (12, 16, 5), (16, 4, 9)]:
+        rp, col = inputs.rmat_csr(scale, deg, seed)
+        got = fora.hot_nodes(rp, col)
+        want = _hot_reference(col, len(rp) - 1)
+        np.testing.assert_array_equal(got, want)
+        assert 0 < len(got) <= 128
+    # a star: every leaf points at the hub (in-degree 300), the hub at leaf 1
+    n = 301
+    col = np.concatenate([[1], np.zeros(n - 1, dtype=np.int32)]).astype(np.int32)
+    rp = np.arange(n + 1, dtype=np.int64)
+    np.testing.assert_array_equal(fora.hot_nodes(rp, col), [0])
+    # 200 nodes tied at in-degree 100 (more than 128): all left out
+    n = 200
+    col = np.tile(np.arange(n, dtype=np.int32), 100)
+    rp = np.arange(0, 100 * n + 1, 100, dtype=np.int64)
+    assert len(fora.hot_nodes(rp, col)) == 0
+    # 100 of 200 nodes tied at in-degree 100 (fewer than 128), the rest at 0: all 100 kept
+    col = np.tile(np.arange(100, dtype=np.int32), 100)
+    rp = np.arange(0, len(col) + 1, 50, dtype=np.int64)  # 200 rows of 50 edges
+    np.testing.assert_array_equal(fora.hot_nodes(rp, col), np.arange(100))
+    # no node reaches in-degree 64
+    rp, col = np.arange(11, dtype=np.int64), np.arange(1, 11, dtype=np.int32) % 10
+    assert len(fora.hot_nodes(rp, col)) == 0
+    # bad arguments
+    import ctypes
+    c = ctypes.c_int32()
+    assert lib.fora_hot_nodes(0, None, None, None, 0, ctypes.byref(c)) == fora.FORA_ERR_BAD_ARG
+    bad = np.array([0, 5], dtype=np.int32)
+    rp2 = np.array([0, 1, 2], dtype=np.int64)
+    assert lib.fora_hot_nodes(2, rp2.ctypes.data, bad.ctypes.data, None, 0,
+                              ctypes.byref(c)) == fora.FORA_ERR_BAD_ARG

@@ -6,6 +6,9 @@
 // the frontier is grouped by source without a global sort.  Round t:
 //   k_push_spread   r(u) += inc_v for every out-edge (v, u) of F_t: FP64 reductions
 //                   that return nothing, so a warp never waits on an atomic.
+//                   (k_push_spread_hot, the default on graphs with hot nodes, first
+//                   sums a block's pushes to the few nodes of highest in-degree in
+//                   shared memory; see there.)
 //   k_push_take     F_{t+1} = {u : r(u) > r_max * d(u)} over the sources that pushed in
 //                   round t (every other r is unchanged and below its threshold), in one
 //                   streaming pass over their residues; each crossing node is appended

@@ -13,9 +13,12 @@ node without out-edges, rows sorted ascending.
 from __future__ import annotations
 
 import ctypes
+import hashlib
+import json
 import os
 import subprocess
 import threading
+import zlib
 
 import numpy as np
 
@@ -63,9 +66,84 @@ def _load():
     return _lib
 
 
+_CACHE_MAGIC = b"RMATCSR1"
+
+
+def _cache_key(scale, avg_deg, seed, abcd):
+    """Parameters of a generated graph and their hash (names its cache file)."""
+    params = {"scale": int(scale), "avg_deg": float(avg_deg), "seed": int(seed),
+              "abcd": [float(x) for x in abcd], "generator": "rmat.c"}
+    text = json.dumps(params, sort_keys=True)
+    return params, hashlib.sha256(text.encode()).hexdigest()[:16]
+
+
+def _cache_read(path, params):
+    """(row_ptr, col) from a cache file whose header matches params and whose arrays
+    match the header's sizes and CRC-32; None otherwise."""
+    try:
+        with open(path, "rb") as f:
+            if f.read(len(_CACHE_MAGIC)) != _CACHE_MAGIC:
+                return None
+            hlen = int.from_bytes(f.read(8), "little")
+            if not 0 < hlen < 1 << 16:
+                return None
+            head = json.loads(f.read(hlen).decode())
+            if head.get("params") != params:
+                return None
+            n, m = int(head["n"]), int(head["m"])
+            row_ptr = np.fromfile(f, dtype=np.int64, count=n + 1)
+            col = np.fromfile(f, dtype=np.int32, count=m)
+    except (OSError, ValueError, KeyError):
+        return None
+    if len(row_ptr) != n + 1 or len(col) != m:
+        return None
+    crc = zlib.crc32(col.view(np.uint8), zlib.crc32(row_ptr.view(np.uint8)))
+    if crc != head.get("crc32") or row_ptr[0] != 0 or row_ptr[-1] != m:
+        return None
+    return row_ptr, col
+
+
+def _cache_write(path, params, row_ptr, col):
+    """Write the cache file atomically (a temporary name, then a rename)."""
+    crc = zlib.crc32(col.view(np.uint8), zlib.crc32(row_ptr.view(np.uint8)))
+    head = json.dumps({"params": params, "n": len(row_ptr) - 1, "m": len(col),
+                       "crc32": crc}).encode()
+    tmp = path + f".tmp{os.getpid()}"
+    with open(tmp, "wb") as f:
+        f.write(_CACHE_MAGIC)
+        f.write(len(head).to_bytes(8, "little"))
+        f.write(head)
+        row_ptr.tofile(f)
+        col.tofile(f)
+    os.replace(tmp, path)
+
+
 def rmat_csr(scale: int, avg_deg: float, seed: int, abcd=RMAT_ABCD,
-             nthreads: int | None = None):
-    """Return ``(row_ptr int64[n+1], col int32[m])`` of a seeded R-MAT graph."""
+             nthreads: int | None = None, cache_dir: str | None = None):
+    """Return ``(row_ptr int64[n+1], col int32[m])`` of a seeded R-MAT graph.
+
+    With ``cache_dir`` (default: the directory in ``FORA_GRAPH_CACHE``, if set) the graph
+    is kept there as a binary CSR file behind a header holding the generator's parameters
+    and a CRC-32 of the arrays, named by a hash of the parameters; a file whose header or
+    checksum does not match is regenerated.  Generation is deterministic, so a cached
+    graph equals a generated one."""
+    if cache_dir is None:
+        cache_dir = os.environ.get("FORA_GRAPH_CACHE") or None
+    path = params = None
+    if cache_dir:
+        params, key = _cache_key(scale, avg_deg, seed, abcd)
+        path = os.path.join(cache_dir, f"rmat_{int(scale)}_{key}.csr")
+        got = _cache_read(path, params)
+        if got is not None:
+            return got
+    row_ptr, col = _generate(scale, avg_deg, seed, abcd, nthreads)
+    if path:
+        os.makedirs(cache_dir, exist_ok=True)
+        _cache_write(path, params, row_ptr, col)
+    return row_ptr, col
+
+
+def _generate(scale, avg_deg, seed, abcd, nthreads):
     lib = _load()
     a, b, c, _ = abcd
     if nthreads is None:

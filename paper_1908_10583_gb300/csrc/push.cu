@@ -387,7 +387,7 @@ __device__ __forceinline__ void hot_slice(const GraphDev& g, double* r, unsigned
   }
 }
 
-// Light rounds: the tiles of the targets of up to 32 pushes (act) are marked.
+// Light rounds: the take tile of this lane's push target is marked (when act).
 __device__ __forceinline__ void hot_mark(const GraphDev& g, const BatchDev& b, int cs,
                                          uint32_t code, bool act) {
   const unsigned long long n = (unsigned long long)g.n;
